@@ -1,0 +1,201 @@
+"""Pins for the oracle's colouring, rational nodes and multi-shift CG.
+
+Each check is against something other than the oracle itself: closed-form
+colourings, a brute-force distance pattern, scipy.linalg.logm, Jacobi-function
+identities, dense complex solves, and the full-probing invariant
+(Sec. 2.1: sum_j e_j^T log(Q) e_j = tr log Q).
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from oracle import closed_forms as cf
+from oracle import hht
+from oracle import matrices as om
+from oracle import method as mt
+from oracle import probing
+from oracle.cgm import cgm
+
+
+# ---------------------------------------------------------------- colouring
+def path_graph(n):
+    return sp.diags([np.full(n - 1, -1.0), np.full(n, 2.5), np.full(n - 1, -1.0)], [-1, 0, 1]).tocsr()
+
+
+@pytest.mark.parametrize("d", [0, 1, 2, 3, 5])
+def test_path_colouring_is_i_mod_d_plus_1(d):
+    col = probing.colour_greedy(path_graph(23), d)
+    assert np.array_equal(col, np.arange(23) % (d + 1))
+
+
+def test_grid_distance_one_is_checkerboard():
+    Q = om.precision(om.KIND_2D5, (9, 7), 0.5)
+    col = probing.colour_greedy(Q, 1).reshape(7, 9)
+    y, x = np.mgrid[0:7, 0:9]
+    assert np.array_equal(col, (x + y) % 2)
+
+
+def test_full_probing_when_distance_exceeds_diameter():
+    Q = om.precision(om.KIND_2D5, (5, 4), 0.5)
+    col = probing.colour_greedy(Q, 7)   # diameter = 4 + 3
+    assert np.array_equal(np.sort(col), np.arange(20))
+
+
+@pytest.mark.parametrize("kind,dims,per,d", [
+    (om.KIND_2D5, (40, 33), False, 4),
+    (om.KIND_2D5, (64, 64), True, 4),
+    (om.KIND_2D13_SQ, (30, 31), False, 2),
+    (om.KIND_3D7, (9, 8, 7), False, 3),
+])
+def test_colouring_valid_and_class_sum(kind, dims, per, d):
+    Q = om.precision(kind, dims, 0.5, periodic=per)
+    col = probing.colour_greedy(Q, d)
+    assert probing.is_valid_colouring(Q, d, col)
+    V = probing.probing_vectors(col)
+    assert np.array_equal(V.sum(axis=1), np.ones(Q.shape[0]))
+
+
+def test_colour_count_independent_of_grid_size():
+    """Sec. 3: the number of colours barely depends on the discretisation."""
+    counts = [int(probing.colour_greedy(om.precision(om.KIND_2D5, (s, s), 0.5), 4).max()) + 1
+              for s in (32, 64, 128)]
+    assert max(counts) - min(counts) <= 2
+
+
+def test_invalid_colouring_detected():
+    Q = om.precision(om.KIND_2D5, (6, 6), 0.5)
+    col = probing.colour_greedy(Q, 2)
+    col[7] = col[8]
+    assert not probing.is_valid_colouring(Q, 2, col)
+
+
+# ---------------------------------------------------------------- nodes
+def test_jacobi_identities_complex():
+    m = 0.37
+    x = np.linspace(-1.5, 1.5, 11)
+    sn, cn, dn = hht.jacobi_complex(x, 0.6, m)
+    assert np.allclose(sn ** 2 + cn ** 2, 1, atol=1e-13)
+    assert np.allclose(dn ** 2 + m * sn ** 2, 1, atol=1e-13)
+    # d sn / dt = cn dn along the real direction
+    e = 1e-6
+    snp, _, _ = hht.jacobi_complex(x + e, 0.6, m)
+    snm, _, _ = hht.jacobi_complex(x - e, 0.6, m)
+    assert np.allclose((snp - snm) / (2 * e), cn * dn, atol=1e-8)
+
+
+@pytest.mark.parametrize("N", [12, 20])
+def test_rational_log_matches_logm(N):
+    g = np.random.default_rng(0)
+    B = g.standard_normal((40, 40))
+    A = B @ B.T / 40 + 0.3 * np.eye(40)
+    lam = np.linalg.eigvalsh(A)
+    s, a = hht.log_nodes(lam.min(), lam.max(), N)
+    F = sum(np.real(al * np.linalg.inv(A - si * np.eye(40))) for si, al in zip(s, a))
+    err = np.abs(F - sla.logm(A)).max()
+    assert err <= 200 * hht.rate_bound(lam.min(), lam.max(), N) + 1e-13
+
+
+@pytest.mark.parametrize("m,M,N", [(0.5, 8.5, 8), (0.5, 8.5, 16), (1e-4, 64.2, 20),
+                                   (1e-4, 64.2, 32), (0.01, 12.0, 10)])
+def test_certificate_follows_two_pi_squared_rate(m, M, N):
+    """Error decays like exp(-2 pi^2 N/(log(M/m)+6)) (constant < 200), far faster
+    than the exp(-2 pi N/(...)) the paper prints."""
+    s, a = hht.log_nodes(m, M, N)
+    cert = hht.certificate(m, M, s, a)
+    assert cert <= 200 * hht.rate_bound(m, M, N) + 2e-15
+    printed = np.exp(-2 * np.pi * N / (np.log(M / m) + 6))
+    assert cert < printed
+
+
+def test_nodes_enclose_spectrum_and_avoid_negative_axis():
+    s, a = hht.log_nodes(0.5, 8.5, 20)
+    w = np.sqrt(s)
+    assert np.all(np.imag(s) > 0)            # upper half of the contour
+    assert np.all(np.real(w) > 0)
+
+
+# ---------------------------------------------------------------- CG-M
+def test_cgm_matches_dense_complex_solves():
+    Q = om.precision(om.KIND_2D5, (10, 9), 0.5)
+    A = Q.toarray()
+    lmin, lmax = mt.spectral_bounds(om.KIND_2D5, (10, 9), 0.5)
+    sigma, alpha = hht.log_nodes(lmin, lmax, 12)
+    g = np.random.default_rng(1)
+    v = (g.random(90) < 0.2).astype(float)
+    res = cgm(Q.dot, v, -sigma, 1e-13, 1000, keep_vectors=True)
+    for l, sg in enumerate(sigma):
+        x = np.linalg.solve(A - sg * np.eye(90), v.astype(complex))
+        assert np.abs(res["xs"][l] - x).max() <= 1e-10 * np.abs(x).max()
+        assert abs(res["pi"][l] - v @ x) <= 1e-10 * abs(v @ x)
+    x0 = np.linalg.solve(A, v)
+    assert np.abs(res["x0"] - x0).max() <= 1e-10 * np.abs(x0).max()
+
+
+def test_cgm_projected_equals_vector_form():
+    Q = om.precision(om.KIND_2D13_SQ, (12, 11), 0.1)
+    lmin, lmax = mt.spectral_bounds(om.KIND_2D13_SQ, (12, 11), 0.1)
+    sigma, _ = hht.log_nodes(lmin, lmax, 16)
+    v = np.zeros(132)
+    v[::7] = 1.0
+    res = cgm(Q.dot, v, -sigma, 1e-12, 5000, keep_vectors=True)
+    proj_from_vec = res["xs"] @ v
+    assert np.abs(res["pi"] - proj_from_vec).max() <= 1e-11 * np.abs(proj_from_vec).max()
+
+
+def test_cgm_detects_indefinite():
+    from oracle.cgm import NotSPD
+    A = sp.diags([1.0, 2.0, -1.0]).tocsr()
+    with pytest.raises(NotSPD):
+        cgm(A.dot, np.ones(3), np.array([0.1 + 0.1j]), 1e-10, 100)
+
+
+def test_spectral_bounds_enclose_closed_form_spectrum():
+    for kind, dims, per in [(om.KIND_2D5, (64, 64), True), (om.KIND_2D5, (31, 17), False),
+                            (om.KIND_2D13_SQ, (40, 40), False), (om.KIND_3D7, (7, 6, 5), False)]:
+        lo, hi = mt.spectral_bounds(kind, dims, 0.2, periodic=per)
+        elo, ehi = cf.extreme_eigs(kind, dims, 0.2, per)
+        assert lo <= elo * (1 + 1e-12) and hi >= ehi * (1 - 1e-12)
+        assert abs(lo - elo) <= 1e-12 * elo and abs(hi - ehi) <= 1e-12 * ehi
+
+
+# ---------------------------------------------------------------- method end to end
+def test_full_probing_method_equals_exact_logdet():
+    """d >= diameter gives unit vectors: the probed value is tr log Q exactly; the
+    method then differs only by quadrature and CG tolerance."""
+    dims = (6, 5)
+    Q = om.precision(om.KIND_2D5, dims, 0.5)
+    col = probing.colour_greedy(Q, 20)
+    lo, hi = mt.spectral_bounds(om.KIND_2D5, dims, 0.5)
+    res = mt.logdet_method(Q, col, lo, hi, 20, 1e-12)
+    exact = cf.logdet(om.KIND_2D5, dims, 0.5, False)
+    assert abs(res["logdet"] - exact) <= 1e-9 * abs(exact)
+
+
+def test_method_equals_exact_rational_target():
+    """CG-M probed value == exact banded solves of the same shifted systems."""
+    dims = (16, 14)
+    mask = np.zeros(224, np.uint8)
+    mask[::9] = 1
+    Q = om.precision(om.KIND_2D5, dims, 0.1, tau=4.0, mask=mask)
+    col = probing.colour_greedy(Q, 4)
+    lo, hi = mt.spectral_bounds(om.KIND_2D5, dims, 0.1, tau=4.0, mask=mask)
+    res = mt.logdet_method(Q, col, lo, hi, 20, 1e-12, per_colour=True)
+    exact_terms = mt.probed_rational_band(Q, col, res["sigma"], res["alpha"], per_colour=True)
+    assert np.abs(res["terms"] - exact_terms).max() <= 1e-9 * np.abs(exact_terms).max()
+    # and the rational target is within quadrature error of the exact probed log
+    pd = mt.probed_dense(Q, col, np.log)
+    cert = hht.certificate(lo, hi, res["sigma"], res["alpha"])
+    assert abs(float(exact_terms.sum()) - pd) <= 224 * cert + 1e-9
+
+
+def test_probing_error_shrinks_with_distance():
+    """Sec. 3 / Table 1 trend: larger colouring distance, closer to exact."""
+    dims = (48, 48)
+    Q = om.precision(om.KIND_2D5, dims, 0.05, periodic=True)
+    exact = cf.logdet(om.KIND_2D5, dims, 0.05, True)
+    errs = []
+    for d in (2, 4, 6, 8):
+        col = probing.colour_greedy(Q, d)
+        errs.append(abs(cf.probed_value(om.KIND_2D5, dims, 0.05, True, col, np.log) - exact))
+    assert all(e2 < e1 for e1, e2 in zip(errs, errs[1:]))
