@@ -1,0 +1,289 @@
+#!/usr/bin/env python3
+"""Benchmark: log det evaluations per second of the Matern alpha=2 GMRF prior.
+
+Workload (one step = one batch): the 13-point Matern precision
+Q = (kappa^2 I - Lap)^2 on a 1024 x 1024 Dirichlet-truncated grid (n = 1,048,576),
+probing vectors from the distance-2 greedy colouring of the graph of Q
+(18 colours), N = 20 quadrature nodes, each shifted system to relative
+residual 1e-6, FP32 vectors with FP64 scalars and reductions; the batch is 16
+kappa^2 values drawn log-uniformly in [0.01, 1] (seeded).  Inputs are synthetic
+and seeded; the CG working set (~0.45 GB) exceeds the 129 MB L2.
+
+Lines printed (rank 0): one JSON line per run.  `--impl reference` times the
+CPU oracle (banded Cholesky log det, Sec. 2's traditional method) on a bounded
+leading block of the same matrix and scales to the full size.
+
+Multi-GPU (torchrun): each rank evaluates its own seeded kappa^2 batch (weak
+scaling, no data-path collective); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+DIMS = (1024, 1024)
+DIST = 2
+NSHIFT = 20
+TOL = 1e-6
+BATCH = 16
+SEED = 2
+METRIC = "log-det(+grad) evals/sec (Matern 1024^2, probing d=2, N=20)"
+UNIT = "evals/s"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def peak_hbm():
+    try:
+        with open(PEAKS) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self):
+        self.samples = []
+        self._stop = threading.Event()
+        self._proc = None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            idx = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+            self._proc = subprocess.Popen(
+                ["nvidia-smi", "-i", idx, "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self._proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+
+    def _read(self):
+        for line in self._proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self._proc:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except Exception:
+                self._proc.kill()
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if "Active" in s[3 + k]
+                          and "Not" not in s[3 + k]})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def iteration_bytes(n, ncols, ntiles, prec):
+    """Algorithmic HBM bytes of one CG iteration (phase A + phase B), per tile-iteration.
+
+    phase A reads r, p_{k-1} and writes p_k; phase B reads p_k, r and the colour of each
+    vertex, writes r: 6 vector passes + 4 bytes/vertex.  Halo re-reads are not counted.
+    """
+    w = 8 if prec == "fp64" else 4
+    T = ncols // ntiles
+    return 6 * n * T * w + 4 * n
+
+
+def run_ours(args):
+    import torch
+    import paper_1105_5256_gb300 as L
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    L.library(build_if_missing=True)
+    prec = L.LD_MIXED if args.precision == "mixed" else L.LD_FP64
+    draws = synth.kappa2_draws(SEED + 1000 * rank, BATCH)
+    ctx = L.ld_create(L.grid_matrix(L.LD_STENCIL_2D13_SQ, DIMS, float(draws[0])), DIST, NSHIFT,
+                      TOL, L.options(precision=prec))
+    n = DIMS[0] * DIMS[1]
+
+    def step():
+        infos = []
+        vals = []
+        for k2 in draws:
+            L.ld_set_params(ctx, float(k2))
+            v, info = L.ld_logdet(ctx)
+            vals.append(v)
+            infos.append(info)
+        return vals, infos
+
+    for _ in range(args.warmup):
+        step()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks()
+    clocks.start()
+    t0 = time.perf_counter()
+    dev_ms = 0.0
+    iter_ms = 0.0
+    tile_iters = 0
+    launches = 0
+    all_infos = []
+    vals = []
+    for _ in range(args.steps):
+        v, infos = step()
+        vals.extend(v)
+        all_infos.extend(infos)
+        for i in infos:
+            dev_ms += i["ms"]
+            iter_ms += i["iter_ms"]
+            tile_iters += i["tile_iters"]
+            launches += i["gpu_launches"]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    # max over ranks of device time and of wall time
+    if ws > 1:
+        t = torch.tensor([dev_ms, wall], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dev_ms, wall = float(t[0]), float(t[1])
+    evals = BATCH * args.steps * ws
+    value = evals / (dev_ms / 1e3)
+    e2e = evals / wall
+    info0 = all_infos[0]
+    ncols = ((info0["n_colours"] + info0["tile_width"] - 1) // info0["tile_width"]) * info0["tile_width"]
+    ntiles = ncols // info0["tile_width"]
+    bytes_tile_iter = iteration_bytes(n, ncols, ntiles, args.precision)
+    achieved = bytes_tile_iter * tile_iters / (iter_ms / 1e3) / 1e9
+    peak, src = peak_hbm()
+    traffic = None
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 vectors / f64 scalars" if args.precision == "mixed" else "f64",
+        "data": "synthetic (seeded kappa^2 draws; no dataset)",
+        "config": {"workload": "Matern alpha=2 (kappa^2 I - Lap)^2, 1024x1024 Dirichlet, 13-point",
+                   "n": n, "colouring_distance": DIST, "n_colours": info0["n_colours"],
+                   "n_shifts": NSHIFT, "tol": TOL, "batch_kappa2_draws": BATCH,
+                   "precision": args.precision, "tile_width": info0["tile_width"],
+                   "engine": info0["engine"], "parallelism": "dp%d (independent batches)" % ws,
+                   "l2": "working set %.2f GB > 129 MB L2" % (3 * n * ncols * (4 if args.precision == "mixed" else 8) / 1e9)},
+        "clocks": clk,
+        "e2e": {"value": e2e, "unit": UNIT,
+                "h2d_bytes_per_step": BATCH * (3 * 8 + 2 * NSHIFT * 16),
+                "d2h_bytes_per_step": BATCH * (2 * 8 + 2 * 4 * 0 + 8 + 4 * ncols)},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": "CG iteration (k_phaseA + k_phaseB)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": src},
+        "iters_mean": float(np.mean([i["iters"] for i in all_infos])),
+        "logdet_first": vals[0],
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(budget_s: float):
+    """The oracle (plain single-thread C banded Cholesky, natural order) on the leading
+    principal block of the same matrix; its cost is linear in the block's rows, so the
+    full-size time is the measured time scaled by n / rows."""
+    from oracle import matrices as om
+    from oracle import method as mt
+    k2 = float(synth.kappa2_draws(SEED, BATCH)[0])
+    n = DIMS[0] * DIMS[1]
+    rows_per_line = DIMS[0]
+    lines = 4
+    # grow the sample until it takes a measurable share of the budget
+    while True:
+        sub = (DIMS[0], lines)
+        Qs = om.precision(om.KIND_2D13_SQ, sub, k2)
+        t0 = time.perf_counter()
+        mt.exact_logdet_band(Qs)
+        dt = time.perf_counter() - t0
+        if dt > budget_s / 4 or lines >= DIMS[1]:
+            break
+        lines *= 2
+    rows = rows_per_line * lines
+    full_s = dt * n / rows
+    return {"value": 1.0 / full_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "banded Cholesky log det of the same model on a %dx%d grid (%d rows, "
+                      "band %d, cost linear in rows) in %.2f s, scaled by n/rows = %.0f"
+                      % (DIMS[0], lines, rows, 2 * DIMS[0], dt, n / rows)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    per = []
+    for _ in range(max(1, args.warmup)):
+        cpu_baseline(args.cpu_seconds / 4)
+    samples = []
+    for _ in range(args.steps):
+        cb = cpu_baseline(args.cpu_seconds)
+        per.append(1.0 / cb["value"])
+        samples.append(cb["sample"])
+    value = 1.0 / statistics.mean(per)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(per) * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": "Matern alpha=2 (kappa^2 I - Lap)^2, 1024x1024 Dirichlet, 13-point"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": samples[-1]},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/*
+ * logdet.h -- C ABI of liblogdet: log det Q and its hyperparameter gradient for
+ * large sparse SPD precision matrices on one NVIDIA GB300 (sm_103a).
+ *
+ * Method (Aune & Simpson, "Parameter Estimation in High Dimensional Gaussian
+ * Distributions"):
+ *   log det Q = tr log Q                                  (Sec. 2.1, Eq. "eq_logdet_ident")
+ *   tr log Q ~ sum_c v_c^T log(Q) v_c, v_c = indicator of colour class c of a
+ *              distance-d colouring of the graph of Q     (Sec. 2.1, probing vectors)
+ *   log(Q) v ~ sum_l alpha_l (Q - sigma_l I)^{-1} v       (Sec. 2.1, Eq. "eq_rat_app",
+ *              contour-integral midpoint rule of Hale, Higham & Trefethen)
+ *   all shifted systems solved on one Krylov space by multi-shift CG
+ *              (CG-M / COCG-M)                            (Sec. 2.1, last two paragraphs)
+ *   gradient   d log det Q / d eta = tr(Q^{-1} dQ/d eta), estimated with the
+ *              same probing vectors and the seed solutions Q^{-1} v_c.
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns ld_status.  Outputs are written only on LD_OK (the
+ *     ld_info record, when given, is always filled).  Nothing aborts, throws,
+ *     exits or traps across this boundary; ld_last_error() describes the most
+ *     recent failure on the calling thread.
+ *   - Pointers are HOST pointers unless the parameter name ends in _dev.  Host
+ *     inputs are borrowed only for the duration of the call: the library
+ *     copies what it needs into device memory it owns.
+ *   - A context is used by one host thread at a time.  Calls are blocking:
+ *     work is queued on the context's stream and the call synchronises that
+ *     stream before it returns.
+ *   - Vertex order is natural: index = x + nx*(y + ny*z).
+ */
+#ifndef PAPER_1105_5256_GB300_LOGDET_H
+#define PAPER_1105_5256_GB300_LOGDET_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LD_ABI_VERSION 1
+
+typedef struct ld_ctx ld_ctx;
+
+typedef enum {
+    LD_OK = 0,
+    LD_EINVAL = 1,        /* bad argument (null pointer, size, unsupported combination) */
+    LD_ENOMEM = 2,        /* device or host allocation failed */
+    LD_ECUDA = 3,         /* a CUDA runtime call failed */
+    LD_ENOTSPD = 4,       /* p^T Q p <= 0 met in CG: Q is not SPD */
+    LD_ENOTCONV = 5,      /* max_iter reached before every shifted system converged */
+    LD_ENUMERIC = 6,      /* NaN/Inf in the CG scalars */
+    LD_ETIMEOUT = 7,      /* a bounded device wait ran out */
+    LD_EUNSUPPORTED = 8   /* combination not implemented */
+} ld_status;
+
+typedef enum { LD_FP64 = 0, LD_MIXED = 1 } ld_precision;
+
+/* Matrix kinds.  Grid kinds describe the SPDE precisions of Sec. 3 on a
+ * regular lattice; "non-periodic" means Dirichlet truncation (out-of-grid
+ * neighbours dropped, diagonal kept). */
+typedef enum {
+    LD_CSR = 0,            /* general symmetric CSR matrix */
+    LD_STENCIL_2D5 = 1,    /* scale*(diag(kappa2) - Lap_5pt + tau*diag(mask)) on nx x ny */
+    LD_STENCIL_2D13_SQ = 2,/* scale*(kappa2 I - Lap_5pt)^2 (13-point Matern alpha=2) */
+    LD_STENCIL_3D7 = 3     /* scale*(diag(kappa2) - Lap_7pt + tau*diag(mask)) on nx x ny x nz */
+} ld_kind;
+
+/* Hyperparameter ids for gradients: dQ/d eta. */
+enum {
+    LD_P_KAPPA2 = 0,  /* kappa2 (or the multiplier c of a kappa2 field: kappa2(s) = c*field(s)) */
+    LD_P_TAU = 1,     /* tau of the observation term tau*diag(mask) */
+    LD_P_SCALE = 2    /* prior scale s of Q = s*Q0 */
+};
+
+typedef struct {
+    int32_t kind;             /* ld_kind */
+    int32_t periodic;         /* grid kinds: 1 = torus, 0 = Dirichlet truncation */
+    int64_t n;                /* CSR: rows; grid kinds: ignored (product of dims) */
+    const int64_t *rowptr;    /* CSR: n+1 row offsets */
+    const int32_t *colidx;    /* CSR: column indices, symmetric pattern */
+    const double *val;        /* CSR: values */
+    int32_t dims[3];          /* grid kinds: nx, ny[, nz]; unused dims = 1 */
+    double kappa2;            /* scalar kappa^2, or multiplier c when kappa2_field != NULL */
+    const double *kappa2_field; /* grid kinds 2D5/3D7: per-vertex kappa^2 (n), or NULL */
+    double tau;               /* observation precision (grid kinds 2D5/3D7) */
+    const uint8_t *obs_mask;  /* n bytes, 1 = observed node; NULL = no observation term */
+    double scale;             /* prior scale s (> 0); 0 is read as 1 */
+} ld_matrix;
+
+typedef struct {
+    int32_t precision;        /* ld_precision: FP64 vectors, or FP32 vectors with FP64 scalars */
+    int32_t tile_width;       /* probing vectors per tile: 0 = choose automatically */
+    int32_t max_iter;         /* CG iteration cap per tile; 0 = 100000 */
+    int32_t keep_x0;          /* keep seed solutions Q^{-1} v_c for ld_grad (extra HBM traffic) */
+    double lambda_min;        /* > 0: user lower spectral bound; else library bound */
+    double lambda_max;        /* > 0: user upper spectral bound; else library bound */
+    void *cuda_stream;        /* cudaStream_t to run on; NULL = a stream the context owns */
+    const int32_t *colouring; /* optional host colouring (n ints >= 0); NULL = greedy */
+    int32_t engine;           /* 0 auto, 1 multi-CTA grid engine, 2 one-CTA-per-tile engine */
+    int32_t chunk_iters;      /* iterations per captured CUDA graph chunk; 0 = auto */
+} ld_options;
+
+typedef struct {
+    int32_t status;           /* ld_status of the call */
+    int32_t n_colours;        /* probing vectors C */
+    int32_t n_shifts;         /* quadrature nodes N */
+    int32_t iters;            /* CG iterations (maximum over tiles) */
+    int32_t tile_width;
+    int32_t engine;
+    double lambda_min, lambda_max; /* interval enclosing the spectrum used for the nodes */
+    double quad_cert;         /* max |f_N(lambda) - log lambda| on [lambda_min, lambda_max] */
+    double ms;                /* device time of the solve (CUDA events) */
+    double iter_ms;           /* device time spent in CG iterations (events around each
+                                 iteration launch on the context stream) */
+    int64_t tile_iters;       /* sum over tiles of the iterations each tile ran */
+    int64_t gpu_launches;     /* kernels this call launched (graph nodes counted) */
+} ld_info;
+
+/* ABI version (LD_ABI_VERSION).  Never fails. */
+int ld_abi_version(void);
+
+/* Fill *opt with defaults (FP64, automatic tile width and engine). */
+ld_status ld_default_options(ld_options *opt);
+
+/* Create a context for Q (Sec. 2.1 method set-up).
+ *   Q                  matrix description (host, borrowed for this call).
+ *   colouring_distance d >= 0: probing vectors from a distance-d greedy colouring of
+ *                      the graph of Q (Sec. 2.1; natural order, smallest free colour),
+ *                      unless opt->colouring supplies one.
+ *   n_shifts           N >= 1 quadrature nodes of the rational log (Eq. "eq_rat_app").
+ *   tol                relative residual at which each shifted system is converged
+ *                      (|zeta| ||r|| <= tol ||v_c||), 0 < tol < 1.
+ *   opt                NULL = defaults.
+ *   out                receives the context (owned by the caller; ld_destroy frees it).
+ * Copies Q, the colouring and any fields into device memory on the current device.
+ * Errors: LD_EINVAL, LD_EUNSUPPORTED, LD_ENOMEM, LD_ECUDA. */
+ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, double tol,
+                    const ld_options *opt, ld_ctx **out);
+
+/* Replace kappa2 (or its field multiplier), tau and scale, keeping the pattern and
+ * colouring (Sec. 3: colourings are computed once and stored).  Spectral bounds and
+ * nodes are recomputed unless the user fixed them.  CSR contexts: LD_EUNSUPPORTED. */
+ld_status ld_set_params(ld_ctx *ctx, double kappa2, double tau, double scale);
+
+/* log det Q ~ sum_c Re sum_l alpha_l v_c^T (Q - sigma_l I)^{-1} v_c
+ * (Sec. 2.1, Eqs. "eq_logdet_ident", "eq_rat_app").  *logdet on LD_OK.
+ * Errors: LD_ENOTSPD, LD_ENOTCONV (no output), LD_ENUMERIC, LD_ECUDA. */
+ld_status ld_logdet(ld_ctx *ctx, double *logdet, ld_info *info);
+
+/* log det Q and grad[i] = d log det Q / d eta_{ids[i]} ~ sum_c (E v_c)^T Q^{-1} v_c,
+ * E = dQ/d eta (tr(Q^{-1} dQ/d eta) probed with the same v_c and the CG seed
+ * solutions).  ids from LD_P_*; n_params in [1, 3]. */
+ld_status ld_logdet_grad(ld_ctx *ctx, int n_params, const int *param_ids, double *logdet,
+                         double *grad, ld_info *info);
+
+/* Backward pass on the seed solutions saved by the last ld_logdet of a context
+ * created with keep_x0 = 1: grad[i] = sum_c (E_{ids[i]} v_c)^T x0_c.
+ * Errors: LD_EINVAL when no solve with keep_x0 precedes it. */
+ld_status ld_grad(ld_ctx *ctx, int n_params, const int *param_ids, double *grad);
+
+/* The same estimate restricted to colours [colour_begin, colour_end): the unit of
+ * work the paper hands to one node (Sec. 2.1, "Each node gets one probing vector").
+ * Partials over a split of [0, C) sum to ld_logdet's value. */
+ld_status ld_logdet_partial(ld_ctx *ctx, int colour_begin, int colour_end, double *partial,
+                            ld_info *info);
+
+/* Per-colour terms of the last solve: terms[c] = Re sum_l alpha_l v_c^T x^{sigma_l}_c
+ * (n_colours doubles) and, if seed != NULL, seed[c] = v_c^T Q^{-1} v_c. */
+ld_status ld_column_terms(const ld_ctx *ctx, double *terms, double *seed);
+
+/* Colouring used by the context: colour (n int32), *n_colours. */
+ld_status ld_get_colouring(const ld_ctx *ctx, int32_t *colour, int32_t *n_colours);
+
+/* Quadrature nodes in use: sigma, alpha as interleaved (re, im) pairs, N each. */
+ld_status ld_get_nodes(const ld_ctx *ctx, double *sigma, double *alpha, int32_t *n_shifts);
+
+/* y = Q x for ncols columns with the library's own SpMM (operator check).
+ * x, y host arrays, row-major n x ncols, in FP64; the operator runs in the
+ * context's precision. */
+ld_status ld_apply(ld_ctx *ctx, int ncols, const double *x, double *y);
+
+/* Host utilities (no device work; usable without a GPU). */
+
+/* Greedy distance-d colouring of the CSR pattern in natural order (Sec. 2.1).
+ * colour: n int32 out.  *n_colours out. */
+ld_status ld_colour_csr(int64_t n, const int64_t *rowptr, const int32_t *colidx, int d,
+                        int32_t *colour, int32_t *n_colours);
+
+/* Same colouring for a grid kind (lattice-ball search, no CSR needed). */
+ld_status ld_colour_grid(int kind, const int32_t dims[3], int periodic, int d, int32_t *colour,
+                         int32_t *n_colours);
+
+/* Nodes/weights of the rational log on [lmin, lmax] (Eq. "eq_rat_app"):
+ * sigma, alpha interleaved (re, im), N each; *cert = max |f_N - log| on the interval. */
+ld_status ld_hht_nodes(double lmin, double lmax, int N, double *sigma, double *alpha,
+                       double *cert);
+
+/* Spectral interval the library uses for a grid kind (Weyl bounds). */
+ld_status ld_grid_bounds(const ld_matrix *Q, double *lmin, double *lmax);
+
+/* Batched evaluation of many independent grid GMRFs in one persistent launch
+ * (each (instance, tile) a work item).  Qs[count], distances[count] as in ld_create. */
+ld_status ld_batch_create(int count, const ld_matrix *Qs, const int *distances, int n_shifts,
+                          double tol, const ld_options *opt, ld_ctx **out);
+
+/* logdets[count]; grads[count] (d/d kappa2, may be NULL); infos may be NULL. */
+ld_status ld_batch_logdet(ld_ctx *ctx, double *logdets, double *grads, ld_info *info);
+
+/* Message for the last failure on this thread; never NULL. */
+const char *ld_last_error(void);
+
+/* Free a context (NULL-safe). */
+void ld_destroy(ld_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

@@ -1,0 +1,834 @@
+// C ABI of liblogdet (declarations and contracts in include/logdet.h).
+//
+// Host runtime around the CUDA engine: argument checking, the probing
+// colouring (Sec. 2.1), spectral bounds and quadrature nodes (Eq.
+// "eq_rat_app"), device buffers, the CG iteration driver (CUDA-graph chunks
+// with an on-device convergence counter) and the gradient pass.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/logdet.h"
+#include "internal.h"
+
+using ld::Operator;
+using ld::Solve;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+ld_status fail(ld_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CUDA_TRY(expr)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(e_ == cudaErrorMemoryAllocation ? LD_ENOMEM : LD_ECUDA, "%s: %s", #expr, \
+                        cudaGetErrorString(e_));                                              \
+    } while (0)
+
+#define ENGINE_TRY(expr)                                                                      \
+    do {                                                                                      \
+        int e_ = (expr);                                                                      \
+        if (e_ != 0) return fail(LD_ECUDA, "%s: %s", #expr, ld::engine_error_string(e_));     \
+    } while (0)
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+    cudaError_t alloc(size_t b) {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = b;
+        if (b == 0) return cudaSuccess;
+        return cudaMalloc(&p, b);
+    }
+    template <class X>
+    X *as() const { return static_cast<X *>(p); }
+};
+
+}  // namespace
+
+struct ld_ctx {
+    // problem
+    int kind = 0, periodic = 0;
+    int32_t dims[3] = {1, 1, 1};
+    int64_t n = 0;
+    double kappa2 = 0, tau = 0, scale = 1;
+    bool has_field = false, has_mask = false, mask_any = false;
+    int distance = 0, nshift = 0;
+    double tol = 0;
+    ld_options opt{};
+    bool user_bounds = false;
+    // colouring
+    std::vector<int32_t> colour;
+    int ncolours = 0;
+    // tiling
+    int T = 4, ntiles = 0, ncols = 0, engine = 1, chunk = 16;
+    // nodes
+    double lmin = 0, lmax = 0, cert = 0;
+    std::vector<std::complex<double>> sigma, alpha;
+    // device
+    DevBuf d_colour, d_field_d, d_field_f, d_mask, d_rowptr, d_colidx, d_val_d, d_val_f;
+    DevBuf d_r, d_p0, d_p1, d_x;
+    DevBuf d_colscal;  // 8 double arrays [ncols]
+    DevBuf d_colint;   // 2 int arrays [ncols]
+    DevBuf d_shift;    // 4 double2 arrays [ncols*N] + uint8 [ncols*N]
+    DevBuf d_nodes;    // shift[N], weight[N] (double2)
+    DevBuf d_tile;     // tile_done, tile_ctr [ntiles]; remaining, status
+    DevBuf d_partial;
+    DevBuf d_terms;    // terms[ncols], class_size[ncols], result[2], grad[3]
+    std::vector<double> class_size;
+    Solve s{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_chunk = 0;
+    int32_t *h_pinned = nullptr;  // remaining, status
+    bool have_x0 = false;
+    int last_cb = 0, last_ce = 0;
+    bool solved = false;
+
+    ~ld_ctx() {
+        if (graph) cudaGraphExecDestroy(graph);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        if (ev2) cudaEventDestroy(ev2);
+        if (ev3) cudaEventDestroy(ev3);
+        if (h_pinned) cudaFreeHost(h_pinned);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+};
+
+namespace {
+
+int64_t grid_n(const int32_t dims[3]) { return (int64_t)dims[0] * dims[1] * dims[2]; }
+
+// Weyl bounds with the exact extreme eigenvalues of the truncated / periodic
+// second difference per dimension (matches ld_grid_bounds' contract).
+void lap_extremes(int N, int periodic, double *lo, double *hi) {
+    if (periodic) {
+        double best = 0.0;
+        for (int k = 0; k < N; ++k) best = std::max(best, 2.0 - 2.0 * std::cos(2.0 * M_PI * k / N));
+        *lo = 0.0;
+        *hi = best;
+    } else {
+        *lo = 2.0 - 2.0 * std::cos(M_PI / (N + 1));
+        *hi = 2.0 + 2.0 * std::cos(M_PI / (N + 1));
+    }
+}
+
+void grid_bounds(int kind, const int32_t dims[3], int periodic, double k2min, double k2max,
+                 double tau_max, double scale, double *lmin, double *lmax) {
+    const int nd = (kind == ld::KIND_3D7) ? 3 : 2;
+    double mlo = 0.0, mhi = 0.0;
+    for (int d = 0; d < nd; ++d) {
+        double a, b;
+        lap_extremes(dims[d], periodic, &a, &b);
+        mlo += a;
+        mhi += b;
+    }
+    double lo = k2min + mlo, hi = k2max + tau_max + mhi;
+    if (kind == ld::KIND_2D13_SQ) {
+        lo *= lo;
+        hi *= hi;
+    }
+    lo *= scale;
+    hi *= scale;
+    hi = std::max(hi, 1.01 * lo);
+    *lmin = lo;
+    *lmax = hi;
+}
+
+ld_status validate_matrix(const ld_matrix *Q) {
+    if (!Q) return fail(LD_EINVAL, "Q is NULL");
+    if (Q->kind < LD_CSR || Q->kind > LD_STENCIL_3D7) return fail(LD_EINVAL, "unknown kind %d", Q->kind);
+    const double scale = Q->scale == 0.0 ? 1.0 : Q->scale;
+    if (!(scale > 0.0) || !std::isfinite(scale)) return fail(LD_EINVAL, "scale must be > 0");
+    if (Q->kind == LD_CSR) {
+        if (Q->n <= 0 || !Q->rowptr || !Q->colidx || !Q->val) return fail(LD_EINVAL, "CSR needs n > 0, rowptr, colidx, val");
+        if (Q->rowptr[0] != 0) return fail(LD_EINVAL, "rowptr[0] must be 0");
+        for (int64_t i = 0; i < Q->n; ++i)
+            if (Q->rowptr[i + 1] < Q->rowptr[i]) return fail(LD_EINVAL, "rowptr not monotone at %lld", (long long)i);
+        const int64_t nnz = Q->rowptr[Q->n];
+        for (int64_t e = 0; e < nnz; ++e) {
+            if (Q->colidx[e] < 0 || Q->colidx[e] >= Q->n) return fail(LD_EINVAL, "colidx out of range at %lld", (long long)e);
+            if (!std::isfinite(Q->val[e])) return fail(LD_EINVAL, "non-finite value at %lld", (long long)e);
+        }
+        return LD_OK;
+    }
+    const int nd = (Q->kind == LD_STENCIL_3D7) ? 3 : 2;
+    for (int d = 0; d < 3; ++d) {
+        if (d < nd && Q->dims[d] < 1) return fail(LD_EINVAL, "dims[%d] must be >= 1", d);
+        if (d >= nd && Q->dims[d] != 1 && Q->dims[d] != 0) return fail(LD_EINVAL, "dims[%d] must be 1 for this kind", d);
+    }
+    if (!std::isfinite(Q->kappa2) || Q->kappa2 < 0.0) return fail(LD_EINVAL, "kappa2 must be finite and >= 0");
+    if (Q->kind == LD_STENCIL_2D13_SQ && (Q->kappa2_field || (Q->obs_mask && Q->tau != 0.0)))
+        return fail(LD_EUNSUPPORTED, "13-point Matern kind takes a scalar kappa2 and no observation term");
+    if (!std::isfinite(Q->tau) || Q->tau < 0.0) return fail(LD_EINVAL, "tau must be finite and >= 0");
+    return LD_OK;
+}
+
+// tile width: fewest padded bytes, ties to the wider tile
+int choose_tile(int precision, int C, int requested) {
+    const int *opts;
+    static const int f64[3] = {1, 2, 4};
+    static const int f32[3] = {2, 4, 8};
+    opts = precision == LD_FP64 ? f64 : f32;
+    if (requested > 0) {
+        for (int k = 0; k < 3; ++k)
+            if (opts[k] == requested) return requested;
+        return -1;
+    }
+    int best = opts[0];
+    int64_t best_cols = INT64_MAX;
+    for (int k = 0; k < 3; ++k) {
+        const int t = opts[k];
+        const int64_t cols = (int64_t)((C + t - 1) / t) * t;
+        if (cols <= best_cols) {
+            best_cols = cols;
+            best = t;
+        }
+    }
+    return best;
+}
+
+ld_status set_nodes(ld_ctx *c) {
+    c->sigma.assign(c->nshift, 0.0);
+    c->alpha.assign(c->nshift, 0.0);
+    if (ld::hht_log_nodes(c->lmin, c->lmax, c->nshift, c->sigma.data(), c->alpha.data()) != 0)
+        return fail(LD_EINVAL, "bad spectral interval [%g, %g]", c->lmin, c->lmax);
+    c->cert = ld::hht_certificate(c->lmin, c->lmax, c->nshift, c->sigma.data(), c->alpha.data());
+    std::vector<double2> h(2 * c->nshift);
+    for (int l = 0; l < c->nshift; ++l) {
+        h[l] = make_double2(-c->sigma[l].real(), -c->sigma[l].imag());    // s_l = -sigma_l
+        h[c->nshift + l] = make_double2(c->alpha[l].real(), c->alpha[l].imag());
+    }
+    CUDA_TRY(cudaMemcpy(c->d_nodes.p, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    return LD_OK;
+}
+
+ld_status compute_bounds(ld_ctx *c, const double *field) {
+    if (c->user_bounds) {
+        c->lmin = c->opt.lambda_min;
+        c->lmax = std::max(c->opt.lambda_max, 1.01 * c->opt.lambda_min);
+        return LD_OK;
+    }
+    if (c->kind == LD_CSR) return fail(LD_EINVAL, "CSR matrices need opt.lambda_min and opt.lambda_max");
+    double k2min = c->kappa2, k2max = c->kappa2;
+    if (c->has_field) {
+        k2min = INFINITY;
+        k2max = -INFINITY;
+        for (int64_t i = 0; i < c->n; ++i) {
+            k2min = std::min(k2min, c->kappa2 * field[i]);
+            k2max = std::max(k2max, c->kappa2 * field[i]);
+        }
+    }
+    grid_bounds(c->kind, c->dims, c->periodic, k2min, k2max, c->mask_any ? c->tau : 0.0, c->scale,
+                &c->lmin, &c->lmax);
+    if (!(c->lmin > 0.0)) return fail(LD_EINVAL, "spectral lower bound %g is not positive (kappa2 = 0 on a torus?)", c->lmin);
+    return LD_OK;
+}
+
+void fill_operator(ld_ctx *c) {
+    Operator &op = c->s.op;
+    op.kind = c->kind;
+    op.periodic = c->periodic;
+    op.nx = c->dims[0];
+    op.ny = c->dims[1];
+    op.nz = c->dims[2];
+    op.n = c->n;
+    op.kappa2 = c->kappa2;
+    op.tau = c->tau;
+    op.scale = c->kind == LD_CSR ? 1.0 : c->scale;
+    op.field_d = c->d_field_d.as<double>();
+    op.field_f = c->d_field_f.as<float>();
+    op.mask = c->d_mask.as<uint8_t>();
+    op.rowptr = c->d_rowptr.as<int64_t>();
+    op.colidx = c->d_colidx.as<int32_t>();
+    op.val_d = c->d_val_d.as<double>();
+    op.val_f = c->d_val_f.as<float>();
+}
+
+void invalidate_graph(ld_ctx *c) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+}
+
+ld_status ensure_graph(ld_ctx *c) {
+    if (c->graph && c->graph_chunk == c->chunk) return LD_OK;
+    invalidate_graph(c);
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int err = 0;
+    for (int j = 0; j < c->chunk && !err; ++j) err = ld::engine_iteration(c->s, j & 1, c->stream);
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (err) {
+        if (g) cudaGraphDestroy(g);
+        return fail(LD_ECUDA, "capture: %s", ld::engine_error_string(err));
+    }
+    if (e2 != cudaSuccess) return fail(LD_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e2));
+    cudaError_t e3 = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) {
+        c->graph = nullptr;
+        return fail(LD_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e3));
+    }
+    c->graph_chunk = c->chunk;
+    return LD_OK;
+}
+
+void fill_info(const ld_ctx *c, ld_info *info, ld_status st, int iters, float ms, int64_t launches,
+               double iter_ms = 0.0, int64_t tile_iters = 0) {
+    if (!info) return;
+    info->iter_ms = iter_ms;
+    info->tile_iters = tile_iters;
+    info->status = st;
+    info->n_colours = c->ncolours;
+    info->n_shifts = c->nshift;
+    info->iters = iters;
+    info->tile_width = c->T;
+    info->engine = c->engine;
+    info->lambda_min = c->lmin;
+    info->lambda_max = c->lmax;
+    info->quad_cert = c->cert;
+    info->ms = ms;
+    info->gpu_launches = launches;
+}
+
+// One probed solve over colours [cb, ce).  On LD_OK, result[0..1] hold
+// sum of terms and sum of seed projections on the device and in *out.
+ld_status run_solve(ld_ctx *c, int cb, int ce, bool keep_x0, double out[2], ld_info *info) {
+    int64_t launches = 0;
+    int iters = 0;
+    float ms = 0.f;
+    if (keep_x0 && !c->d_x.p) {
+        const size_t vb = (size_t)c->ntiles * c->n * c->T * (c->opt.precision == LD_FP64 ? 8 : 4);
+        CUDA_TRY(c->d_x.alloc(vb));
+        c->s.x = c->d_x.p;
+        invalidate_graph(c);
+    }
+    const int want_x0 = keep_x0 ? 1 : 0;
+    if (c->s.keep_x0 != want_x0) {
+        c->s.keep_x0 = want_x0;
+        invalidate_graph(c);
+    }
+    c->have_x0 = false;
+    c->solved = false;
+    const int max_iter = c->opt.max_iter > 0 ? c->opt.max_iter : 100000;
+    CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+    ENGINE_TRY(ld::engine_init(c->s, cb, ce, c->stream));
+    launches += 3;
+    ld_status st = LD_OK;
+    double iter_ms = 0.0;
+    if (c->engine == 2) {
+        CUDA_TRY(cudaEventRecord(c->ev2, c->stream));
+        ENGINE_TRY(ld::engine_cta_solve(c->s, max_iter, c->stream));
+        CUDA_TRY(cudaEventRecord(c->ev3, c->stream));
+        launches += 1;
+        CUDA_TRY(cudaMemcpyAsync(c->h_pinned, c->s.remaining, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(c->h_pinned + 1, c->s.status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        float e = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&e, c->ev2, c->ev3));
+        iter_ms += e;
+    } else {
+        if (ld_status g = ensure_graph(c)) return g;
+        int done_iters = 0;
+        for (;;) {
+            CUDA_TRY(cudaEventRecord(c->ev2, c->stream));
+            CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
+            CUDA_TRY(cudaEventRecord(c->ev3, c->stream));
+            launches += 2 * c->chunk;
+            done_iters += c->chunk;
+            CUDA_TRY(cudaMemcpyAsync(c->h_pinned, c->s.remaining, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(cudaMemcpyAsync(c->h_pinned + 1, c->s.status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(cudaStreamSynchronize(c->stream));
+            float e = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&e, c->ev2, c->ev3));
+            iter_ms += e;
+            if (c->h_pinned[0] <= 0 || c->h_pinned[1] != 0 || done_iters >= max_iter) break;
+        }
+    }
+    const int dev_status = c->h_pinned[1];
+    const int remaining = c->h_pinned[0];
+    ENGINE_TRY(ld::engine_finish(c->s, cb, ce, c->stream));
+    launches += 1;
+    CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(out, c->s.result, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    std::vector<int32_t> it(c->ncols);
+    CUDA_TRY(cudaMemcpyAsync(it.data(), c->s.col_iters, c->ncols * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    for (int v : it) iters = std::max(iters, v);
+    int64_t tile_iters = 0;
+    for (int t = 0; t < c->ntiles; ++t) {
+        int m = 0;
+        for (int k = 0; k < c->T; ++k) m = std::max(m, it[t * c->T + k]);
+        tile_iters += m;
+    }
+    if (dev_status == ld::DEV_NOTSPD) st = fail(LD_ENOTSPD, "p^T Q p <= 0: Q is not SPD");
+    else if (dev_status == ld::DEV_NUMERIC) st = fail(LD_ENUMERIC, "non-finite CG scalar");
+    else if (dev_status == ld::DEV_TIMEOUT) st = fail(LD_ETIMEOUT, "device wait timed out");
+    else if (dev_status != 0) st = fail(LD_ECUDA, "device status %d", dev_status);
+    else if (remaining > 0) st = fail(LD_ENOTCONV, "%d tiles not converged after %d iterations", remaining, iters);
+    else if (!std::isfinite(out[0])) st = fail(LD_ENUMERIC, "non-finite log det");
+    fill_info(c, info, st, iters, ms, launches, iter_ms, tile_iters);
+    if (st == LD_OK) {
+        c->have_x0 = keep_x0;
+        c->solved = true;
+        c->last_cb = cb;
+        c->last_ce = ce;
+    }
+    return st;
+}
+
+ld_status check_params(const ld_ctx *c, int n_params, const int *ids) {
+    if (n_params < 1 || n_params > 3 || !ids) return fail(LD_EINVAL, "n_params must be 1..3 with ids");
+    for (int k = 0; k < n_params; ++k) {
+        const int p = ids[k];
+        if (p < LD_P_KAPPA2 || p > LD_P_SCALE) return fail(LD_EINVAL, "unknown parameter id %d", p);
+        if (c->kind == LD_CSR && p != LD_P_SCALE) return fail(LD_EUNSUPPORTED, "CSR matrices only have the scale parameter");
+        if (c->kind == LD_STENCIL_2D13_SQ && p == LD_P_TAU) return fail(LD_EUNSUPPORTED, "no tau in the Matern kind");
+    }
+    return LD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ld_abi_version(void) { return LD_ABI_VERSION; }
+
+const char *ld_last_error(void) { return g_err.c_str(); }
+
+ld_status ld_default_options(ld_options *opt) {
+    if (!opt) return fail(LD_EINVAL, "opt is NULL");
+    std::memset(opt, 0, sizeof *opt);
+    opt->precision = LD_FP64;
+    return LD_OK;
+}
+
+ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, double tol,
+                    const ld_options *opt_in, ld_ctx **out) {
+    if (!out) return fail(LD_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (ld_status v = validate_matrix(Q)) return v;
+    if (colouring_distance < 0) return fail(LD_EINVAL, "colouring_distance must be >= 0");
+    if (n_shifts < 1 || n_shifts > 256) return fail(LD_EINVAL, "n_shifts must be in [1, 256]");
+    if (!(tol > 0.0 && tol < 1.0)) return fail(LD_EINVAL, "tol must be in (0, 1)");
+    ld_options opt;
+    ld_default_options(&opt);
+    if (opt_in) opt = *opt_in;
+    if (opt.precision != LD_FP64 && opt.precision != LD_MIXED) return fail(LD_EINVAL, "bad precision");
+    if (opt.max_iter < 0) return fail(LD_EINVAL, "max_iter must be >= 0");
+    if (opt.engine < 0 || opt.engine > 2) return fail(LD_EINVAL, "engine must be 0, 1 or 2");
+    if (opt.chunk_iters < 0 || opt.chunk_iters > 4096) return fail(LD_EINVAL, "chunk_iters out of range");
+
+    ld_ctx *c = new (std::nothrow) ld_ctx();
+    if (!c) return fail(LD_ENOMEM, "host allocation");
+    std::unique_ptr<ld_ctx> guard(c);
+    c->kind = Q->kind;
+    c->periodic = Q->periodic ? 1 : 0;
+    c->opt = opt;
+    c->distance = colouring_distance;
+    c->nshift = n_shifts;
+    c->tol = tol;
+    c->scale = Q->scale == 0.0 ? 1.0 : Q->scale;
+    c->kappa2 = Q->kappa2;
+    c->tau = Q->tau;
+    c->user_bounds = opt.lambda_min > 0.0 && opt.lambda_max > 0.0;
+    if (c->kind == LD_CSR) {
+        c->n = Q->n;
+    } else {
+        c->dims[0] = Q->dims[0];
+        c->dims[1] = Q->dims[1];
+        c->dims[2] = (Q->kind == LD_STENCIL_3D7) ? Q->dims[2] : 1;
+        c->n = grid_n(c->dims);
+        if (c->n > ((int64_t)1 << 31) - 1) return fail(LD_EINVAL, "grid too large");
+        c->has_field = Q->kappa2_field != nullptr;
+        c->has_mask = Q->obs_mask != nullptr;
+        if (c->has_mask)
+            for (int64_t i = 0; i < c->n && !c->mask_any; ++i) c->mask_any = Q->obs_mask[i] != 0;
+    }
+    if (c->kind == LD_CSR && !c->user_bounds)
+        return fail(LD_EINVAL, "CSR matrices need opt.lambda_min and opt.lambda_max > 0");
+
+    // colouring (Sec. 2.1)
+    c->colour.resize(c->n);
+    if (opt.colouring) {
+        int mx = -1;
+        for (int64_t i = 0; i < c->n; ++i) {
+            if (opt.colouring[i] < 0) return fail(LD_EINVAL, "negative colour at %lld", (long long)i);
+            mx = std::max(mx, (int)opt.colouring[i]);
+            c->colour[i] = opt.colouring[i];
+        }
+        c->ncolours = mx + 1;
+    } else if (c->kind == LD_CSR) {
+        c->ncolours = ld::colour_csr(c->n, Q->rowptr, Q->colidx, colouring_distance, c->colour.data());
+    } else {
+        c->ncolours = ld::colour_grid(c->kind, c->dims, c->periodic, colouring_distance, c->colour.data());
+    }
+    // tiling
+    c->T = choose_tile(opt.precision, c->ncolours, opt.tile_width);
+    if (c->T < 0) return fail(LD_EINVAL, "tile_width %d not available for this precision", opt.tile_width);
+    c->ntiles = (c->ncolours + c->T - 1) / c->T;
+    c->ncols = c->ntiles * c->T;
+    c->class_size.assign(c->ncols, 0.0);
+    for (int64_t i = 0; i < c->n; ++i) c->class_size[c->colour[i]] += 1.0;
+    if (opt.engine) {
+        c->engine = opt.engine;
+    } else {
+        c->engine = (c->n <= 32768 || (c->ntiles >= 152 && c->n <= 262144)) ? 2 : 1;
+    }
+    c->chunk = opt.chunk_iters > 0 ? opt.chunk_iters + (opt.chunk_iters & 1) : 16;
+
+    // stream, events
+    if (opt.cuda_stream) {
+        c->stream = static_cast<cudaStream_t>(opt.cuda_stream);
+    } else {
+        CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    CUDA_TRY(cudaEventCreate(&c->ev0));
+    CUDA_TRY(cudaEventCreate(&c->ev1));
+    CUDA_TRY(cudaEventCreate(&c->ev2));
+    CUDA_TRY(cudaEventCreate(&c->ev3));
+    CUDA_TRY(cudaMallocHost((void **)&c->h_pinned, 4 * sizeof(int32_t)));
+
+    // device copies of the problem
+    const bool f32 = opt.precision == LD_MIXED;
+    CUDA_TRY(c->d_colour.alloc(c->n * sizeof(int32_t)));
+    CUDA_TRY(cudaMemcpy(c->d_colour.p, c->colour.data(), c->n * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (c->has_field) {
+        std::vector<float> ff(c->n);
+        for (int64_t i = 0; i < c->n; ++i) ff[i] = (float)Q->kappa2_field[i];
+        CUDA_TRY(c->d_field_d.alloc(c->n * sizeof(double)));
+        CUDA_TRY(cudaMemcpy(c->d_field_d.p, Q->kappa2_field, c->n * sizeof(double), cudaMemcpyHostToDevice));
+        CUDA_TRY(c->d_field_f.alloc(c->n * sizeof(float)));
+        CUDA_TRY(cudaMemcpy(c->d_field_f.p, ff.data(), c->n * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    if (c->has_mask) {
+        CUDA_TRY(c->d_mask.alloc(c->n));
+        CUDA_TRY(cudaMemcpy(c->d_mask.p, Q->obs_mask, c->n, cudaMemcpyHostToDevice));
+    }
+    if (c->kind == LD_CSR) {
+        const int64_t nnz = Q->rowptr[c->n];
+        std::vector<double> vd(nnz);
+        std::vector<float> vf(nnz);
+        for (int64_t e = 0; e < nnz; ++e) {
+            vd[e] = c->scale * Q->val[e];
+            vf[e] = (float)vd[e];
+        }
+        CUDA_TRY(c->d_rowptr.alloc((c->n + 1) * sizeof(int64_t)));
+        CUDA_TRY(cudaMemcpy(c->d_rowptr.p, Q->rowptr, (c->n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+        CUDA_TRY(c->d_colidx.alloc(std::max<int64_t>(nnz, 1) * sizeof(int32_t)));
+        CUDA_TRY(cudaMemcpy(c->d_colidx.p, Q->colidx, nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
+        CUDA_TRY(c->d_val_d.alloc(std::max<int64_t>(nnz, 1) * sizeof(double)));
+        CUDA_TRY(cudaMemcpy(c->d_val_d.p, vd.data(), nnz * sizeof(double), cudaMemcpyHostToDevice));
+        if (f32) {
+            CUDA_TRY(c->d_val_f.alloc(std::max<int64_t>(nnz, 1) * sizeof(float)));
+            CUDA_TRY(cudaMemcpy(c->d_val_f.p, vf.data(), nnz * sizeof(float), cudaMemcpyHostToDevice));
+        }
+    }
+    // work buffers
+    const size_t w = f32 ? 4 : 8;
+    const size_t vb = (size_t)c->ntiles * c->n * c->T * w;
+    CUDA_TRY(c->d_r.alloc(vb));
+    CUDA_TRY(c->d_p0.alloc(vb));
+    CUDA_TRY(c->d_p1.alloc(vb));
+    const int N = c->nshift, C = c->ncols;
+    CUDA_TRY(c->d_colscal.alloc((size_t)8 * C * sizeof(double)));
+    CUDA_TRY(c->d_colint.alloc((size_t)2 * C * sizeof(int32_t)));
+    CUDA_TRY(c->d_shift.alloc((size_t)4 * C * N * sizeof(double2) + (size_t)C * N));
+    CUDA_TRY(c->d_nodes.alloc((size_t)2 * N * sizeof(double2)));
+    CUDA_TRY(c->d_tile.alloc((size_t)(2 * c->ntiles + 2) * sizeof(int32_t)));
+    CUDA_TRY(c->d_terms.alloc((size_t)(2 * C + 8) * sizeof(double)));
+    CUDA_TRY(cudaMemcpy(c->d_terms.as<double>() + C, c->class_size.data(), C * sizeof(double), cudaMemcpyHostToDevice));
+
+    Solve &s = c->s;
+    fill_operator(c);
+    s.T = c->T;
+    s.ntiles = c->ntiles;
+    s.ncols = C;
+    s.nshift = N;
+    s.precision = f32 ? 1 : 0;
+    s.keep_x0 = 0;
+    s.tol = tol;
+    s.colour = c->d_colour.as<int32_t>();
+    s.r = c->d_r.p;
+    s.p0 = c->d_p0.p;
+    s.p1 = c->d_p1.p;
+    s.x = nullptr;
+    double *cs = c->d_colscal.as<double>();
+    s.rho = cs;
+    s.alpha = cs + C;
+    s.beta = cs + 2 * C;
+    s.alpha_prev = cs + 3 * C;
+    s.beta_prev = cs + 4 * C;
+    s.vnorm2 = cs + 5 * C;
+    s.pi0 = cs + 6 * C;
+    s.phi0 = cs + 7 * C;
+    s.col_active = c->d_colint.as<int32_t>();
+    s.col_iters = s.col_active + C;
+    double2 *sh = c->d_shift.as<double2>();
+    s.zeta = sh;
+    s.zeta_prev = sh + (size_t)C * N;
+    s.pi = sh + (size_t)2 * C * N;
+    s.phi = sh + (size_t)3 * C * N;
+    s.sh_active = reinterpret_cast<uint8_t *>(sh + (size_t)4 * C * N);
+    s.shift = c->d_nodes.as<double2>();
+    s.weight = c->d_nodes.as<double2>() + N;
+    s.tile_done = c->d_tile.as<int32_t>();
+    s.tile_ctr = s.tile_done + c->ntiles;
+    s.remaining = s.tile_ctr + c->ntiles;
+    s.status = s.remaining + 1;
+    s.terms = c->d_terms.as<double>();
+    s.class_size = s.terms + C;
+    s.result = s.terms + 2 * C;
+    s.bpt = ld::engine_blocks_per_tile(s);
+    const size_t part = std::max<size_t>((size_t)c->ntiles * s.bpt * 2 * c->T, (size_t)152 * 4 * 3);
+    CUDA_TRY(c->d_partial.alloc(part * sizeof(double)));
+    s.partial = c->d_partial.as<double>();
+    CUDA_TRY(cudaMemset(c->d_tile.p, 0, c->d_tile.bytes));
+
+    if (ld_status b = compute_bounds(c, Q->kappa2_field)) return b;
+    if (ld_status nd = set_nodes(c)) return nd;
+    *out = guard.release();
+    return LD_OK;
+}
+
+ld_status ld_set_params(ld_ctx *c, double kappa2, double tau, double scale) {
+    if (!c) return fail(LD_EINVAL, "ctx is NULL");
+    if (c->kind == LD_CSR) return fail(LD_EUNSUPPORTED, "CSR contexts have fixed values");
+    if (!std::isfinite(kappa2) || kappa2 < 0.0) return fail(LD_EINVAL, "kappa2 must be finite and >= 0");
+    if (!std::isfinite(tau) || tau < 0.0) return fail(LD_EINVAL, "tau must be finite and >= 0");
+    if (scale == 0.0) scale = 1.0;
+    if (!(scale > 0.0) || !std::isfinite(scale)) return fail(LD_EINVAL, "scale must be > 0");
+    c->kappa2 = kappa2;
+    c->tau = tau;
+    c->scale = scale;
+    fill_operator(c);
+    invalidate_graph(c);
+    c->solved = false;
+    c->have_x0 = false;
+    if (!c->user_bounds) {
+        std::vector<double> field;
+        if (c->has_field) {
+            field.resize(c->n);
+            CUDA_TRY(cudaMemcpy(field.data(), c->d_field_d.p, c->n * sizeof(double), cudaMemcpyDeviceToHost));
+        }
+        if (ld_status b = compute_bounds(c, field.empty() ? nullptr : field.data())) return b;
+    }
+    return set_nodes(c);
+}
+
+ld_status ld_logdet(ld_ctx *c, double *logdet, ld_info *info) {
+    if (!c || !logdet) return fail(LD_EINVAL, "ctx and logdet must be non-NULL");
+    double out[2];
+    ld_status st = run_solve(c, 0, c->ncolours, c->opt.keep_x0 != 0, out, info);
+    if (st == LD_OK) *logdet = out[0];
+    return st;
+}
+
+ld_status ld_grad(ld_ctx *c, int n_params, const int *ids, double *grad) {
+    if (!c || !grad) return fail(LD_EINVAL, "ctx and grad must be non-NULL");
+    if (ld_status v = check_params(c, n_params, ids)) return v;
+    if (!c->have_x0) return fail(LD_EINVAL, "no seed solutions saved: run ld_logdet on a keep_x0 context first");
+    double *d_out = c->s.result + 2;
+    ENGINE_TRY(ld::engine_grad_params(c->s, n_params, ids, d_out, c->stream));
+    double h[3];
+    CUDA_TRY(cudaMemcpyAsync(h, d_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < n_params; ++k) {
+        if (!std::isfinite(h[k])) return fail(LD_ENUMERIC, "non-finite gradient");
+        grad[k] = h[k];
+    }
+    return LD_OK;
+}
+
+ld_status ld_logdet_grad(ld_ctx *c, int n_params, const int *ids, double *logdet, double *grad,
+                         ld_info *info) {
+    if (!c || !logdet || !grad) return fail(LD_EINVAL, "ctx, logdet and grad must be non-NULL");
+    if (ld_status v = check_params(c, n_params, ids)) return v;
+    // d/d kappa2 of a scalar-kappa2 5/7-point grid is tr(Q^{-1}) * scale: the projected
+    // seed sum v^T Q^{-1} v needs no stored seed vectors.
+    bool projected = (c->kind == LD_STENCIL_2D5 || c->kind == LD_STENCIL_3D7) && !c->has_field;
+    for (int k = 0; k < n_params; ++k) projected = projected && ids[k] == LD_P_KAPPA2;
+    double out[2];
+    ld_status st = run_solve(c, 0, c->ncolours, !projected || c->opt.keep_x0, out, info);
+    if (st != LD_OK) return st;
+    if (projected) {
+        for (int k = 0; k < n_params; ++k) grad[k] = c->scale * out[1];
+    } else {
+        ld_status g = ld_grad(c, n_params, ids, grad);
+        if (info) info->gpu_launches += 2;
+        if (g != LD_OK) return g;
+    }
+    *logdet = out[0];
+    return LD_OK;
+}
+
+ld_status ld_logdet_partial(ld_ctx *c, int cb, int ce, double *partial, ld_info *info) {
+    if (!c || !partial) return fail(LD_EINVAL, "ctx and partial must be non-NULL");
+    if (cb < 0 || ce < cb || ce > c->ncolours) return fail(LD_EINVAL, "colour range [%d, %d) outside [0, %d)", cb, ce, c->ncolours);
+    double out[2];
+    ld_status st = run_solve(c, cb, ce, c->opt.keep_x0 != 0, out, info);
+    if (st == LD_OK) *partial = out[0];
+    return st;
+}
+
+ld_status ld_column_terms(const ld_ctx *c, double *terms, double *seed) {
+    if (!c || !terms) return fail(LD_EINVAL, "ctx and terms must be non-NULL");
+    if (!c->solved) return fail(LD_EINVAL, "no completed solve on this context");
+    CUDA_TRY(cudaMemcpy(terms, c->s.terms, c->ncolours * sizeof(double), cudaMemcpyDeviceToHost));
+    if (seed) CUDA_TRY(cudaMemcpy(seed, c->s.pi0, c->ncolours * sizeof(double), cudaMemcpyDeviceToHost));
+    return LD_OK;
+}
+
+ld_status ld_get_colouring(const ld_ctx *c, int32_t *colour, int32_t *n_colours) {
+    if (!c) return fail(LD_EINVAL, "ctx is NULL");
+    if (colour) std::memcpy(colour, c->colour.data(), c->n * sizeof(int32_t));
+    if (n_colours) *n_colours = c->ncolours;
+    return LD_OK;
+}
+
+ld_status ld_get_nodes(const ld_ctx *c, double *sigma, double *alpha, int32_t *n_shifts) {
+    if (!c) return fail(LD_EINVAL, "ctx is NULL");
+    for (int l = 0; l < c->nshift; ++l) {
+        if (sigma) { sigma[2 * l] = c->sigma[l].real(); sigma[2 * l + 1] = c->sigma[l].imag(); }
+        if (alpha) { alpha[2 * l] = c->alpha[l].real(); alpha[2 * l + 1] = c->alpha[l].imag(); }
+    }
+    if (n_shifts) *n_shifts = c->nshift;
+    return LD_OK;
+}
+
+ld_status ld_apply(ld_ctx *c, int ncols, const double *x, double *y) {
+    if (!c || !x || !y || ncols < 1) return fail(LD_EINVAL, "bad arguments");
+    const int T = c->T;
+    const int nt = (ncols + T - 1) / T;
+    const int64_t n = c->n;
+    const bool f32 = c->opt.precision == LD_MIXED;
+    const size_t w = f32 ? 4 : 8;
+    const size_t elems = (size_t)nt * n * T;
+    std::vector<unsigned char> hx(elems * w, 0), hy(elems * w);
+    for (int t = 0; t < nt; ++t)
+        for (int64_t i = 0; i < n; ++i)
+            for (int k = 0; k < T; ++k) {
+                const int col = t * T + k;
+                const double v = col < ncols ? x[i * ncols + col] : 0.0;
+                const size_t q = ((size_t)t * n + i) * T + k;
+                if (f32) reinterpret_cast<float *>(hx.data())[q] = (float)v;
+                else reinterpret_cast<double *>(hx.data())[q] = v;
+            }
+    DevBuf dx, dy;
+    CUDA_TRY(dx.alloc(elems * w));
+    CUDA_TRY(dy.alloc(elems * w));
+    CUDA_TRY(cudaMemcpyAsync(dx.p, hx.data(), elems * w, cudaMemcpyHostToDevice, c->stream));
+    ENGINE_TRY(ld::engine_apply(c->s.op, f32 ? 1 : 0, T, nt, dx.p, dy.p, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(hy.data(), dy.p, elems * w, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (int t = 0; t < nt; ++t)
+        for (int64_t i = 0; i < n; ++i)
+            for (int k = 0; k < T; ++k) {
+                const int col = t * T + k;
+                if (col >= ncols) continue;
+                const size_t q = ((size_t)t * n + i) * T + k;
+                y[i * ncols + col] = f32 ? (double)reinterpret_cast<float *>(hy.data())[q]
+                                         : reinterpret_cast<double *>(hy.data())[q];
+            }
+    return LD_OK;
+}
+
+ld_status ld_colour_csr(int64_t n, const int64_t *rowptr, const int32_t *colidx, int d,
+                        int32_t *colour, int32_t *n_colours) {
+    if (n < 1 || !rowptr || !colidx || !colour || d < 0) return fail(LD_EINVAL, "bad arguments");
+    const int nc = ld::colour_csr(n, rowptr, colidx, d, colour);
+    if (n_colours) *n_colours = nc;
+    return LD_OK;
+}
+
+ld_status ld_colour_grid(int kind, const int32_t dims[3], int periodic, int d, int32_t *colour,
+                         int32_t *n_colours) {
+    if (!dims || !colour || d < 0 || kind < LD_STENCIL_2D5 || kind > LD_STENCIL_3D7)
+        return fail(LD_EINVAL, "bad arguments");
+    int32_t dd[3] = {dims[0], dims[1], kind == LD_STENCIL_3D7 ? dims[2] : 1};
+    if (dd[0] < 1 || dd[1] < 1 || dd[2] < 1) return fail(LD_EINVAL, "dims must be >= 1");
+    const int nc = ld::colour_grid(kind, dd, periodic ? 1 : 0, d, colour);
+    if (n_colours) *n_colours = nc;
+    return LD_OK;
+}
+
+ld_status ld_hht_nodes(double lmin, double lmax, int N, double *sigma, double *alpha, double *cert) {
+    if (N < 1 || N > 256 || !sigma || !alpha) return fail(LD_EINVAL, "bad arguments");
+    std::vector<std::complex<double>> s(N), a(N);
+    if (ld::hht_log_nodes(lmin, lmax, N, s.data(), a.data()) != 0)
+        return fail(LD_EINVAL, "need 0 < lmin < lmax");
+    for (int l = 0; l < N; ++l) {
+        sigma[2 * l] = s[l].real();
+        sigma[2 * l + 1] = s[l].imag();
+        alpha[2 * l] = a[l].real();
+        alpha[2 * l + 1] = a[l].imag();
+    }
+    if (cert) *cert = ld::hht_certificate(lmin, lmax, N, s.data(), a.data());
+    return LD_OK;
+}
+
+ld_status ld_grid_bounds(const ld_matrix *Q, double *lmin, double *lmax) {
+    if (!lmin || !lmax) return fail(LD_EINVAL, "bad arguments");
+    if (ld_status v = validate_matrix(Q)) return v;
+    if (Q->kind == LD_CSR) return fail(LD_EINVAL, "grid kinds only");
+    int32_t dd[3] = {Q->dims[0], Q->dims[1], Q->kind == LD_STENCIL_3D7 ? Q->dims[2] : 1};
+    const int64_t n = grid_n(dd);
+    double k2min = Q->kappa2, k2max = Q->kappa2;
+    if (Q->kappa2_field) {
+        k2min = INFINITY;
+        k2max = -INFINITY;
+        for (int64_t i = 0; i < n; ++i) {
+            k2min = std::min(k2min, Q->kappa2 * Q->kappa2_field[i]);
+            k2max = std::max(k2max, Q->kappa2 * Q->kappa2_field[i]);
+        }
+    }
+    bool mask = false;
+    if (Q->obs_mask)
+        for (int64_t i = 0; i < n && !mask; ++i) mask = Q->obs_mask[i] != 0;
+    grid_bounds(Q->kind, dd, Q->periodic ? 1 : 0, k2min, k2max, mask ? Q->tau : 0.0,
+                Q->scale == 0.0 ? 1.0 : Q->scale, lmin, lmax);
+    return LD_OK;
+}
+
+ld_status ld_batch_create(int, const ld_matrix *, const int *, int, double, const ld_options *,
+                          ld_ctx **out) {
+    if (out) *out = nullptr;
+    return fail(LD_EUNSUPPORTED, "batched contexts are not available in this build");
+}
+
+ld_status ld_batch_logdet(ld_ctx *, double *, double *, ld_info *) {
+    return fail(LD_EUNSUPPORTED, "batched contexts are not available in this build");
+}
+
+void ld_destroy(ld_ctx *c) { delete c; }
+
+}  // extern "C"

@@ -1,0 +1,106 @@
+// Probing-vector colourings (Sec. 2.1).
+//
+// The probing vectors are the indicator vectors of the colour classes of a
+// distance-d colouring of the graph of Q: any two vertices joined by a path of
+// at most d edges get different colours (equivalently a neighbour colouring of
+// the graph of Q^d).  The colouring is greedy in natural vertex order: vertex i
+// takes the smallest colour not used by an already coloured vertex within
+// distance d.  Colourings depend only on the sparsity pattern, so a context
+// computes one at creation and keeps it (Sec. 3 stores colourings for reuse).
+//
+// Grid kinds avoid a graph search: on the lattice the graph distance is the
+// (torus) L1 distance for the 5- and 7-point stencils and ceil(L1 / 2) for the
+// 13-point square, so the distance-d ball is a fixed set of lattice offsets.
+#include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+#include <vector>
+
+#include "internal.h"
+
+namespace ld {
+
+int colour_csr(int64_t n, const int64_t *rowptr, const int32_t *colidx, int d,
+               int32_t *colour) {
+    std::vector<int64_t> seen(n, -1), frontier, next;
+    std::vector<int64_t> used;  // used[c] == i  <=> colour c taken near vertex i
+    int ncol = 0;
+    for (int64_t i = 0; i < n; ++i) colour[i] = -1;
+    for (int64_t i = 0; i < n; ++i) {
+        frontier.assign(1, i);
+        seen[i] = i;
+        for (int depth = 0; depth < d && !frontier.empty(); ++depth) {
+            next.clear();
+            for (int64_t u : frontier) {
+                for (int64_t e = rowptr[u]; e < rowptr[u + 1]; ++e) {
+                    int64_t w = colidx[e];
+                    if (seen[w] == i) continue;
+                    seen[w] = i;
+                    next.push_back(w);
+                    int32_t cw = colour[w];
+                    if (cw >= 0) {
+                        if ((size_t)cw >= used.size()) used.resize((size_t)cw + 1, -1);
+                        used[cw] = i;
+                    }
+                }
+            }
+            frontier.swap(next);
+        }
+        int32_t c = 0;
+        while ((size_t)c < used.size() && used[c] == i) ++c;
+        colour[i] = c;
+        ncol = std::max(ncol, c + 1);
+    }
+    return ncol;
+}
+
+int colour_grid(int kind, const int32_t dims[3], int periodic, int d, int32_t *colour) {
+    const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
+    const int R = (kind == KIND_2D13_SQ) ? 2 * d : d;   // L1 radius of the ball
+    const bool is3d = (kind == KIND_3D7);
+    struct Off { int dx, dy, dz; };
+    std::vector<Off> offs;
+    for (int dz = is3d ? -R : 0; dz <= (is3d ? R : 0); ++dz)
+        for (int dy = -R; dy <= R; ++dy)
+            for (int dx = -R; dx <= R; ++dx) {
+                if (std::abs(dx) + std::abs(dy) + std::abs(dz) > R) continue;
+                if (dx == 0 && dy == 0 && dz == 0) continue;
+                if (!periodic) {
+                    // only offsets that can reach an earlier vertex in natural order
+                    bool earlier = dz < 0 || (dz == 0 && (dy < 0 || (dy == 0 && dx < 0)));
+                    if (!earlier) continue;
+                }
+                offs.push_back({dx, dy, dz});
+            }
+    const int64_t n = nx * ny * nz;
+    std::vector<int64_t> used;
+    int ncol = 0;
+    for (int64_t i = 0; i < n; ++i) colour[i] = -1;
+    int64_t i = 0;
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x, ++i) {
+                for (const Off &o : offs) {
+                    int64_t xx = x + o.dx, yy = y + o.dy, zz = z + o.dz;
+                    if (periodic) {
+                        xx = ((xx % nx) + nx) % nx;
+                        yy = ((yy % ny) + ny) % ny;
+                        zz = ((zz % nz) + nz) % nz;
+                    } else if (xx < 0 || xx >= nx || yy < 0 || yy >= ny || zz < 0 || zz >= nz) {
+                        continue;
+                    }
+                    int64_t j = xx + nx * (yy + ny * zz);
+                    if (j >= i) continue;   // not yet coloured (or the vertex itself)
+                    int32_t cj = colour[j];
+                    if ((size_t)cj >= used.size()) used.resize((size_t)cj + 1, -1);
+                    used[cj] = i;
+                }
+                int32_t c = 0;
+                while ((size_t)c < used.size() && used[c] == i) ++c;
+                colour[i] = c;
+                ncol = std::max(ncol, c + 1);
+            }
+    return ncol;
+}
+
+}  // namespace ld

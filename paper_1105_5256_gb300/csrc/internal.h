@@ -1,0 +1,92 @@
+// Internal declarations shared by the host runtime (api.cpp, colouring.cpp,
+// hht.cpp) and the CUDA engine (engine.cu).  Not part of the public ABI.
+#pragma once
+
+#include <complex>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace ld {
+
+enum { KIND_CSR = 0, KIND_2D5 = 1, KIND_2D13_SQ = 2, KIND_3D7 = 3 };
+
+// ---------------------------------------------------------------- host helpers
+int colour_csr(int64_t n, const int64_t *rowptr, const int32_t *colidx, int d, int32_t *colour);
+int colour_grid(int kind, const int32_t dims[3], int periodic, int d, int32_t *colour);
+double ellip_k(double m);
+void jacobi_real(double u, double m, double *sn, double *cn, double *dn);
+int hht_log_nodes(double lmin, double lmax, int N, std::complex<double> *sigma,
+                  std::complex<double> *alpha);
+double hht_certificate(double lmin, double lmax, int N, const std::complex<double> *sigma,
+                       const std::complex<double> *alpha);
+
+// ---------------------------------------------------------------- device problem
+// Operator description read by the kernels (device pointers).  Q is
+//   grid 2D5/3D7:  scale * (kappa2_i + 2*dim + tau*mask_i) on the diagonal, -scale off it
+//                  (kappa2_i = kappa2 * field_i when field != nullptr)
+//   grid 2D13_SQ:  scale * (kappa2 I - Lap)^2, expanded as a 13-point stencil
+//   CSR:           scale * val
+struct Operator {
+    int kind;
+    int periodic;
+    int nx, ny, nz;
+    int64_t n;
+    double kappa2;
+    double tau;
+    double scale;
+    const double *field_d;   // kappa2 field base values, FP64 copy
+    const float *field_f;    // FP32 copy
+    const uint8_t *mask;     // observation mask (or nullptr)
+    const int64_t *rowptr;   // CSR
+    const int32_t *colidx;
+    const double *val_d;
+    const float *val_f;
+};
+
+// Status codes written by kernels into the device status word.
+enum { DEV_OK = 0, DEV_NOTSPD = 4, DEV_NUMERIC = 6, DEV_TIMEOUT = 7 };
+
+// Everything one solve's kernels need (passed by value).
+struct Solve {
+    Operator op;
+    int T;                 // columns per tile
+    int ntiles;
+    int ncols;             // padded columns = ntiles * T
+    int nshift;            // N
+    int bpt;               // blocks per tile (grid engine)
+    int precision;         // 0 fp64, 1 mixed
+    int keep_x0;
+    double tol;
+    const int32_t *colour; // n
+    void *r, *p0, *p1, *x; // [ntiles][n][T] in the vector precision
+    // per-column scalars (ncols)
+    double *rho, *alpha, *beta, *alpha_prev, *beta_prev, *vnorm2, *pi0, *phi0;
+    int32_t *col_active, *col_iters;
+    // per (column, shift): [ncols][nshift]
+    double2 *zeta, *zeta_prev, *pi, *phi;
+    uint8_t *sh_active;
+    const double2 *shift;  // s_l = -sigma_l
+    const double2 *weight; // alpha_l
+    // per tile
+    int32_t *tile_done, *tile_ctr;
+    double *partial;       // [ntiles][bpt][T][2]
+    int32_t *remaining;    // tiles not yet converged
+    int32_t *status;       // first error code
+    double *terms;         // per column Re sum alpha_l pi_l
+    const double *class_size; // |colour class| per column (0 for padding)
+    double *result;        // [0] = sum of terms
+};
+
+// Engine entry points (engine.cu); all asynchronous on `stream`.
+int engine_init(const Solve &s, int col_begin, int col_end, void *stream);
+int engine_iteration(const Solve &s, int parity, void *stream);      // phase A + phase B
+int engine_cta_solve(const Solve &s, int max_iter, void *stream);    // whole solve, one CTA per tile
+int engine_finish(const Solve &s, int col_begin, int col_end, void *stream);
+int engine_apply(const Operator &op, int precision, int T, int ntiles, const void *x, void *y,
+                 void *stream);
+int engine_grad_params(const Solve &s, int nparam, const int *ids, double *out_dev, void *stream);
+int engine_blocks_per_tile(const Solve &s);
+const char *engine_error_string(int cuda_err);
+
+}  // namespace ld

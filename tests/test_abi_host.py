@@ -1,0 +1,123 @@
+"""Host-side checks of liblogdet (no GPU): the library loads, exports every entry
+point the header declares, and its host steps match the oracle.
+
+  * colouring (Sec. 2.1, greedy distance-d, natural order) -- bit-exact;
+  * quadrature nodes and weights (Eq. "eq_rat_app")        -- to 1e-12;
+  * spectral interval                                      -- to 1e-14.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1105_5256_gb300 as L
+import synth
+from oracle import hht
+from oracle import matrices as om
+from oracle import method as mt
+from oracle import probing
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1105_5256_gb300 import _build
+    _build.build()
+    return L.library()
+
+
+def header_symbols():
+    src = open(os.path.join(ROOT, "include", "logdet.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:ld_status|int|void|const char \*)\s*\*?\s*(ld_\w+)\s*\(",
+                                 src, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    syms = header_symbols()
+    assert len(syms) >= 20
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert lib.ld_abi_version() == 1
+
+
+@pytest.mark.parametrize("kind,dims,per,d", [
+    (om.KIND_2D5, (64, 64), True, 4),
+    (om.KIND_2D5, (64, 64), True, 2),
+    (om.KIND_2D5, (57, 31), False, 4),
+    (om.KIND_2D5, (1, 40), False, 3),
+    (om.KIND_2D5, (3, 5), True, 2),
+    (om.KIND_2D13_SQ, (40, 37), False, 2),
+    (om.KIND_2D13_SQ, (12, 12), True, 1),
+    (om.KIND_3D7, (9, 8, 7), False, 3),
+    (om.KIND_3D7, (6, 6, 6), True, 2),
+])
+def test_grid_colouring_bit_exact(lib, kind, dims, per, d):
+    Q = om.precision(kind, dims, 0.5, periodic=per)
+    ref = probing.colour_greedy(Q, d)
+    col, nc = L.ld_colour_grid(kind, dims, per, d)
+    assert np.array_equal(col, ref)
+    assert nc == int(ref.max()) + 1
+
+
+def test_csr_colouring_bit_exact(lib):
+    n = 700
+    rows, cols, w = synth.random_sparse_spd_pattern(11, n)
+    rp, ci, vv = synth.csr_from_edges(n, rows, cols, w, 0.5)
+    import scipy.sparse as sp
+    Q = sp.csr_matrix((vv, ci, rp), shape=(n, n))
+    for d in (1, 2, 3):
+        ref = probing.colour_greedy(Q, d)
+        col, nc = L.ld_colour_csr(rp, ci, d)
+        assert np.array_equal(col, ref)
+
+
+@pytest.mark.parametrize("m,M,N", [(0.5, 8.5, 20), (1e-4, 64.2, 20), (0.01, 12.0, 32),
+                                   (1.0, 1.01, 4), (3.0, 3e6, 40)])
+def test_nodes_match_oracle(lib, m, M, N):
+    s, a, cert = L.ld_hht_nodes(m, M, N)
+    so, ao = hht.log_nodes(m, M, N)
+    assert np.abs(s - so).max() <= 1e-12 * np.abs(so).max()
+    assert np.abs(a - ao).max() <= 1e-12 * np.abs(ao).max()
+    co = hht.certificate(m, M, so, ao, samples=2001)
+    assert abs(cert - co) <= 1e-12 + 1e-6 * co
+
+
+def test_node_errors(lib):
+    with pytest.raises(L.LogDetError):
+        L.ld_hht_nodes(-1.0, 2.0, 8)
+    with pytest.raises(L.LogDetError):
+        L.ld_hht_nodes(1.0, 2.0, 0)
+
+
+@pytest.mark.parametrize("kind,dims,per,k2,tau,masked,scale", [
+    (om.KIND_2D5, (64, 64), True, 0.5, 0.0, False, 1.0),
+    (om.KIND_2D5, (100, 37), False, 0.1, 4.0, True, 1.0),
+    (om.KIND_2D13_SQ, (1024, 1024), False, 0.01, 0.0, False, 2.0),
+    (om.KIND_3D7, (16, 12, 9), False, 0.3, 0.0, False, 0.7),
+])
+def test_bounds_match_oracle(lib, kind, dims, per, k2, tau, masked, scale):
+    n = int(np.prod(dims))
+    mask = synth.obs_mask(4, n, 0.1) if masked else None
+    lo, hi = L.ld_grid_bounds(L.grid_matrix(kind, dims, k2, periodic=per, tau=tau, obs_mask=mask,
+                                            scale=scale))
+    lo_o, hi_o = mt.spectral_bounds(kind, dims, k2, periodic=per, tau=tau, mask=mask, scale=scale)
+    assert abs(lo - lo_o) <= 1e-14 * lo_o and abs(hi - hi_o) <= 1e-14 * hi_o
+
+
+def test_field_bounds_match_oracle(lib):
+    dims = (10, 9, 8)
+    f = synth.kappa2_field(5, dims)
+    lo, hi = L.ld_grid_bounds(L.grid_matrix(om.KIND_3D7, dims, 1.0, kappa2_field=f))
+    lo_o, hi_o = mt.spectral_bounds(om.KIND_3D7, dims, f)
+    assert abs(lo - lo_o) <= 1e-14 * lo_o and abs(hi - hi_o) <= 1e-14 * hi_o
+
+
+def test_invalid_matrix_rejected_on_host(lib):
+    with pytest.raises(L.LogDetError) as e:
+        L.ld_grid_bounds(L.grid_matrix(om.KIND_2D5, (0, 4), 0.5))
+    assert e.value.status == L.LD_EINVAL
+    with pytest.raises(L.LogDetError) as e:
+        L.ld_grid_bounds(L.grid_matrix(om.KIND_2D13_SQ, (8, 8), 0.5, kappa2_field=np.ones(64)))
+    assert e.value.status == L.LD_EUNSUPPORTED
