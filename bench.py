@@ -106,10 +106,10 @@ def dist_env():
 
 
 def iteration_bytes(n, ncols, ntiles, prec):
-    """Algorithmic HBM bytes of one CG iteration (phase A + phase B), per tile-iteration.
+    """Algorithmic HBM bytes of one fused CG pass, per tile-iteration.
 
-    phase A reads r, p_{k-1} and writes p_k; phase B reads p_k, r and the colour of each
-    vertex, writes r: 6 vector passes + 4 bytes/vertex.  Halo re-reads are not counted.
+    The pass reads r, w, p of one set and writes r, w, p of the other (6 vector passes of
+    n*T words) and reads each vertex's colour (4 bytes).  Halo re-reads are not counted.
     """
     w = 8 if prec == "fp64" else 4
     T = ncols // ntiles
@@ -129,9 +129,11 @@ def run_ours(args):
         torch.cuda.set_device(0)
     L.library(build_if_missing=True)
     prec = L.LD_MIXED if args.precision == "mixed" else L.LD_FP64
-    draws = synth.kappa2_draws(SEED + 1000 * rank, BATCH)
+    draws = synth.kappa2_draws(SEED + 1000 * rank, args.batch)
+    if args.kappa2 > 0:
+        draws = np.full(args.batch, args.kappa2)
     ctx = L.ld_create(L.grid_matrix(L.LD_STENCIL_2D13_SQ, DIMS, float(draws[0])), DIST, NSHIFT,
-                      TOL, L.options(precision=prec))
+                      TOL, L.options(precision=prec, tile_width=args.tile_width))
     n = DIMS[0] * DIMS[1]
 
     def step():
@@ -177,7 +179,7 @@ def run_ours(args):
         t = torch.tensor([dev_ms, wall], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         dev_ms, wall = float(t[0]), float(t[1])
-    evals = BATCH * args.steps * ws
+    evals = args.batch * args.steps * ws
     value = evals / (dev_ms / 1e3)
     e2e = evals / wall
     info0 = all_infos[0]
@@ -195,16 +197,16 @@ def run_ours(args):
         "data": "synthetic (seeded kappa^2 draws; no dataset)",
         "config": {"workload": "Matern alpha=2 (kappa^2 I - Lap)^2, 1024x1024 Dirichlet, 13-point",
                    "n": n, "colouring_distance": DIST, "n_colours": info0["n_colours"],
-                   "n_shifts": NSHIFT, "tol": TOL, "batch_kappa2_draws": BATCH,
+                   "n_shifts": NSHIFT, "tol": TOL, "batch_kappa2_draws": args.batch,
                    "precision": args.precision, "tile_width": info0["tile_width"],
                    "engine": info0["engine"], "parallelism": "dp%d (independent batches)" % ws,
-                   "l2": "working set %.2f GB > 129 MB L2" % (3 * n * ncols * (4 if args.precision == "mixed" else 8) / 1e9)},
+                   "l2": "CG working set %.2f GB (r, p, p') > 129 MB L2" % (3 * n * ncols * (4 if args.precision == "mixed" else 8) / 1e9)},
         "clocks": clk,
         "e2e": {"value": e2e, "unit": UNIT,
-                "h2d_bytes_per_step": BATCH * (3 * 8 + 2 * NSHIFT * 16),
-                "d2h_bytes_per_step": BATCH * (2 * 8 + 2 * 4 * 0 + 8 + 4 * ncols)},
+                "h2d_bytes_per_step": args.batch * (3 * 8 + 2 * NSHIFT * 16),
+                "d2h_bytes_per_step": args.batch * (2 * 8 + 2 * 4 + 4 * ncols)},
         "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "kernel": "CG iteration (k_phaseA + k_phaseB)",
+        "roofline": {"bound": "hbm", "kernel": "fused CG pass (k_stream2d)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": src},
         "iters_mean": float(np.mean([i["iters"] for i in all_infos])),
@@ -278,6 +280,10 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=BATCH, help="kappa^2 values per step")
+    ap.add_argument("--tile-width", type=int, default=0, help="probing vectors per tile (0 = auto)")
+    ap.add_argument("--kappa2", type=float, default=0.0,
+                    help="fixed kappa^2 for every evaluation (profiling runs); 0 = seeded draws")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

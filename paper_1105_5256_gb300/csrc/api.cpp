@@ -91,12 +91,12 @@ struct ld_ctx {
     std::vector<std::complex<double>> sigma, alpha;
     // device
     DevBuf d_colour, d_field_d, d_field_f, d_mask, d_rowptr, d_colidx, d_val_d, d_val_f;
-    DevBuf d_r, d_p0, d_p1, d_x;
+    DevBuf d_r[2], d_w[2], d_p[2], d_x;
     DevBuf d_colscal;  // 8 double arrays [ncols]
     DevBuf d_colint;   // 2 int arrays [ncols]
     DevBuf d_shift;    // 4 double2 arrays [ncols*N] + uint8 [ncols*N]
     DevBuf d_nodes;    // shift[N], weight[N] (double2)
-    DevBuf d_tile;     // tile_done, tile_ctr [ntiles]; remaining, status
+    DevBuf d_tile;     // tile_done, tile_ctr, tile_par [ntiles]; remaining, status
     DevBuf d_partial;
     DevBuf d_terms;    // terms[ncols], class_size[ncols], result[2], grad[3]
     std::vector<double> class_size;
@@ -191,23 +191,24 @@ ld_status validate_matrix(const ld_matrix *Q) {
     return LD_OK;
 }
 
-// tile width: fewest padded bytes, ties to the wider tile
+// tile width: fewest padded columns; ties go to the narrower tile (8-byte packs
+// keep the streaming pass's registers low and its occupancy high, measured fastest)
 int choose_tile(int precision, int C, int requested) {
     const int *opts;
-    static const int f64[3] = {1, 2, 4};
-    static const int f32[3] = {2, 4, 8};
+    static const int f64[4] = {1, 2, 3, 4};
+    static const int f32[4] = {2, 4, 6, 8};
     opts = precision == LD_FP64 ? f64 : f32;
     if (requested > 0) {
-        for (int k = 0; k < 3; ++k)
+        for (int k = 0; k < 4; ++k)
             if (opts[k] == requested) return requested;
         return -1;
     }
     int best = opts[0];
     int64_t best_cols = INT64_MAX;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 4; ++k) {
         const int t = opts[k];
         const int64_t cols = (int64_t)((C + t - 1) / t) * t;
-        if (cols <= best_cols) {
+        if (cols < best_cols) {
             best_cols = cols;
             best = t;
         }
@@ -361,7 +362,7 @@ ld_status run_solve(ld_ctx *c, int cb, int ce, bool keep_x0, double out[2], ld_i
             CUDA_TRY(cudaEventRecord(c->ev2, c->stream));
             CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
             CUDA_TRY(cudaEventRecord(c->ev3, c->stream));
-            launches += 2 * c->chunk;
+            launches += c->chunk;
             done_iters += c->chunk;
             CUDA_TRY(cudaMemcpyAsync(c->h_pinned, c->s.remaining, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
             CUDA_TRY(cudaMemcpyAsync(c->h_pinned + 1, c->s.status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
@@ -374,6 +375,10 @@ ld_status run_solve(ld_ctx *c, int cb, int ce, bool keep_x0, double out[2], ld_i
     }
     const int dev_status = c->h_pinned[1];
     const int remaining = c->h_pinned[0];
+    if (c->s.keep_x0) {
+        ENGINE_TRY(ld::engine_flush_x(c->s, c->stream));
+        launches += 1;
+    }
     ENGINE_TRY(ld::engine_finish(c->s, cb, ce, c->stream));
     launches += 1;
     CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
@@ -556,15 +561,17 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
     // work buffers
     const size_t w = f32 ? 4 : 8;
     const size_t vb = (size_t)c->ntiles * c->n * c->T * w;
-    CUDA_TRY(c->d_r.alloc(vb));
-    CUDA_TRY(c->d_p0.alloc(vb));
-    CUDA_TRY(c->d_p1.alloc(vb));
+    for (int k = 0; k < 2; ++k) {
+        CUDA_TRY(c->d_r[k].alloc(vb));
+        CUDA_TRY(c->d_w[k].alloc(vb));
+        CUDA_TRY(c->d_p[k].alloc(vb));
+    }
     const int N = c->nshift, C = c->ncols;
     CUDA_TRY(c->d_colscal.alloc((size_t)8 * C * sizeof(double)));
     CUDA_TRY(c->d_colint.alloc((size_t)2 * C * sizeof(int32_t)));
     CUDA_TRY(c->d_shift.alloc((size_t)4 * C * N * sizeof(double2) + (size_t)C * N));
     CUDA_TRY(c->d_nodes.alloc((size_t)2 * N * sizeof(double2)));
-    CUDA_TRY(c->d_tile.alloc((size_t)(2 * c->ntiles + 2) * sizeof(int32_t)));
+    CUDA_TRY(c->d_tile.alloc((size_t)(3 * c->ntiles + 2) * sizeof(int32_t)));
     CUDA_TRY(c->d_terms.alloc((size_t)(2 * C + 8) * sizeof(double)));
     CUDA_TRY(cudaMemcpy(c->d_terms.as<double>() + C, c->class_size.data(), C * sizeof(double), cudaMemcpyHostToDevice));
 
@@ -578,9 +585,11 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
     s.keep_x0 = 0;
     s.tol = tol;
     s.colour = c->d_colour.as<int32_t>();
-    s.r = c->d_r.p;
-    s.p0 = c->d_p0.p;
-    s.p1 = c->d_p1.p;
+    for (int k = 0; k < 2; ++k) {
+        s.rbuf[k] = c->d_r[k].p;
+        s.wbuf[k] = c->d_w[k].p;
+        s.pbuf[k] = c->d_p[k].p;
+    }
     s.x = nullptr;
     double *cs = c->d_colscal.as<double>();
     s.rho = cs;
@@ -603,13 +612,14 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
     s.weight = c->d_nodes.as<double2>() + N;
     s.tile_done = c->d_tile.as<int32_t>();
     s.tile_ctr = s.tile_done + c->ntiles;
-    s.remaining = s.tile_ctr + c->ntiles;
+    s.tile_par = s.tile_ctr + c->ntiles;
+    s.remaining = s.tile_par + c->ntiles;
     s.status = s.remaining + 1;
     s.terms = c->d_terms.as<double>();
     s.class_size = s.terms + C;
     s.result = s.terms + 2 * C;
-    s.bpt = ld::engine_blocks_per_tile(s);
-    const size_t part = std::max<size_t>((size_t)c->ntiles * s.bpt * 2 * c->T, (size_t)152 * 4 * 3);
+    ld::engine_plan(s);
+    const size_t part = std::max<size_t>((size_t)c->ntiles * s.bpt * ld::NDOT * c->T, (size_t)152 * 4 * 3);
     CUDA_TRY(c->d_partial.alloc(part * sizeof(double)));
     s.partial = c->d_partial.as<double>();
     CUDA_TRY(cudaMemset(c->d_tile.p, 0, c->d_tile.bytes));

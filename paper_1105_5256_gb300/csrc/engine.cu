@@ -10,29 +10,18 @@
 //
 // Data layout in HBM: the C probing vectors are padded to ncols = ntiles*T and
 // stored tile-interleaved, [tile][vertex][T]: one vertex's T columns are one
-// 16/32-byte vector, a warp touches 32 consecutive vertices (fully coalesced),
-// and per-vertex data (stencil coefficients, colour, kappa^2 field, mask) is
-// read once per tile.  The SpMM is HBM-bound: no tensor cores (not a dense
-// contraction).
+// 8..32-byte vector, a warp touches 32 consecutive vertices (fully coalesced),
+// and per-vertex data (colour, kappa^2 field, mask) is read once per tile.
+// Columns of a tile iterate in lockstep (each its own CG) until all converge.
+// The SpMM is HBM-bound: no tensor cores (not a dense contraction).
 //
-// Per CG iteration k (all columns of a tile in lockstep, each its own CG):
-//   phase A  p_k = r_k + beta_{k-1} p_{k-1} (formed on the fly, also at the
-//            stencil neighbours), w = Q p_k, store p_k, partial p_k^T w;
-//            the last block of the tile reduces the partials in a fixed order
-//            and sets alpha_k = rho_k / p_k^T Q p_k.
-//   phase B  w = Q p_k recomputed from the stored p_k, r_{k+1} = r_k - alpha_k w,
-//            (x += alpha_k p_k when the seed solution is kept), partials
-//            r^T r and v^T r; the last block runs the scalar tail: beta_k, the
-//            shift recurrences, projections and convergence flags.
-// Traffic per iteration: read r, p_{k-1}, p_k, r; write p_k, r  (6 n T words
-// per tile) plus x in gradient mode.
-//
-// Two engines share these device functions:
-//   grid engine  phases as separate launches, many CTAs per tile, partial
-//                sums reduced by the tile's last CTA; launched in CUDA-graph
-//                chunks by the host.
-//   CTA engine   one CTA runs a tile's whole solve (small problems, batches);
-//                block barriers only.
+// Engines sharing the device functions below:
+//   grid engine   one fused pass per CG iteration (see "fused CG-M pass"),
+//                 many CTAs per tile, partial sums reduced by the tile's last
+//                 CTA, launched by the host in CUDA-graph chunks; the 2D
+//                 lattice kinds use a shared-memory tiled, cp.async-pipelined
+//                 pass kernel, the other kinds a gather kernel.
+//   CTA engine    one CTA runs a tile's whole solve (small problems).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -43,8 +32,13 @@
 namespace ld {
 
 // ------------------------------------------------------------------ packs
+// alignment: largest power of two dividing the pack size, at most 16 bytes
+constexpr int pack_align(int bytes) {
+    return (bytes % 16 == 0) ? 16 : (bytes % 8 == 0) ? 8 : (bytes % 4 == 0) ? 4 : bytes;
+}
+
 template <typename V, int T>
-struct alignas((sizeof(V) * T) >= 16 ? 16 : (sizeof(V) * T)) Pack {
+struct alignas(pack_align(sizeof(V) * T)) Pack {
     V v[T];
 };
 
@@ -58,10 +52,16 @@ __device__ __forceinline__ Pack<V, T> ldg_raw(const Pack<V, T> *p) {
         float4 *o = reinterpret_cast<float4 *>(&out);
 #pragma unroll
         for (int k = 0; k < BYTES / 16; ++k) o[k] = __ldg(q + k);
-    } else if constexpr (BYTES == 8) {
-        *reinterpret_cast<float2 *>(&out) = __ldg(reinterpret_cast<const float2 *>(p));
+    } else if constexpr (BYTES % 8 == 0) {
+        const float2 *q = reinterpret_cast<const float2 *>(p);
+        float2 *o = reinterpret_cast<float2 *>(&out);
+#pragma unroll
+        for (int k = 0; k < BYTES / 8; ++k) o[k] = __ldg(q + k);
     } else {
-        *reinterpret_cast<float *>(&out) = __ldg(reinterpret_cast<const float *>(p));
+        const float *q = reinterpret_cast<const float *>(p);
+        float *o = reinterpret_cast<float *>(&out);
+#pragma unroll
+        for (int k = 0; k < BYTES / 4; ++k) o[k] = __ldg(q + k);
     }
     return out;
 }
@@ -89,20 +89,6 @@ __device__ __forceinline__ void stpack(V *base, int64_t j, const V (&a)[T]) {
 namespace ld {
 
 // ------------------------------------------------------------------ loaders
-// p_k at vertex j formed on the fly from r_k and p_{k-1}.
-template <typename V, int T, bool NC>
-struct LoadRP {
-    const V *r;
-    const V *p;
-    V beta[T];
-    __device__ __forceinline__ void operator()(int64_t j, V (&o)[T]) const {
-        Pack<V, T> a = ldpack<V, T, NC>(r, j);
-        Pack<V, T> b = ldpack<V, T, NC>(p, j);
-#pragma unroll
-        for (int t = 0; t < T; ++t) o[t] = fma(beta[t], b.v[t], a.v[t]);
-    }
-};
-
 template <typename V, int T, bool NC>
 struct LoadP {
     const V *p;
@@ -272,30 +258,6 @@ __device__ __forceinline__ void apply_row(const Operator &op, int64_t i, const L
 }
 
 // ------------------------------------------------------------------ reductions
-template <int K>
-__device__ __forceinline__ void block_sum(double (&v)[K], double *smem /* >= 32*K */) {
-    // warp shuffle tree, then one value per warp through shared memory;
-    // on return thread 0 holds the block sums (fixed order: deterministic).
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    __syncthreads();
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < K; ++k) smem[wid * K + k] = v[k];
-    __syncthreads();
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += smem[w * K + k];
-            v[k] = s;
-        }
-    }
-}
-
 __device__ __forceinline__ void set_status(int32_t *st, int code) { atomicCAS(st, 0, code); }
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
@@ -316,42 +278,79 @@ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double2 cscale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
 __device__ __forceinline__ double cabs2(double2 a) { return hypot(a.x, a.y); }
 
-// Scalar tail of one CG-M iteration for the T columns of `tile`, given the new
-// residual norms rho_{k+1} = r^T r and projections v^T r_{k+1} (sums in
-// sh_rr[t], sh_vr[t]).  Whole block calls it.  Updates beta_k, the seed and
-// shifted projections and the convergence flags; sets tile_done.
-__device__ void scalar_tail(const Solve &s, int tile, const double *sh_rr, const double *sh_vr,
-                            int *sh_any) {
+// ------------------------------------------------------------------ fused CG-M pass
+// One pass per CG iteration k, for every column of a tile (Sec. 2.1: the real
+// seed CG on Q x = v_c drives every shifted system):
+//   r_k = r_{k-1} - alpha_{k-1} w_{k-1}       (alpha, beta from the previous pass)
+//   p_k = r_k + beta_{k-1} p_{k-1}
+//   w_k = Q p_k
+//   dots r.r, p.w, r.w, w.w, v.r, v.w  ->  one reduction
+// and the tail of the pass (last CTA of the tile, FP64):
+//   alpha_k = r.r / p.w
+//   rho_{k+1} = |r_k - alpha_k w_k|^2 = r.r - 2 alpha_k r.w + alpha_k^2 w.w
+//   beta_k = rho_{k+1} / r.r,    v^T r_{k+1} = v.r - alpha_k v.w
+// then the CG-M shift recurrences with (alpha_k, beta_k, v^T r_{k+1}).  The
+// seed solution (gradient mode) gets x += alpha_{k-1} p_{k-1} in the next pass.
+// A pass reads set k&1 of (r, w, p) and writes set (k&1)^1: 3 vector reads and
+// 3 vector writes per iteration, one stencil application, one reduction.
+// The difference-form operator keeps FP32 vectors accurate for ill-conditioned
+// Q; scalars, dot sums across threads and the recurrences are FP64.
+
+// p_k at vertex j from set `cur`: (r - alpha w) + beta p
+template <typename V, int T, bool NC>
+struct LoadFused {
+    const V *r, *w, *p;
+    V a[T], b[T];
+    __device__ __forceinline__ void operator()(int64_t j, V (&o)[T]) const {
+        const Pack<V, T> rr = ldpack<V, T, NC>(r, j), ww = ldpack<V, T, NC>(w, j),
+                         pp = ldpack<V, T, NC>(p, j);
+#pragma unroll
+        for (int t = 0; t < T; ++t) o[t] = fma(b[t], pp.v[t], fma(-a[t], ww.v[t], rr.v[t]));
+    }
+};
+
+// Tail of one pass for the T columns of `tile`; whole block calls it.
+// sums[k*T + t] = dot k of column t (order: rr, pw, rw, ww, vr, vw).
+__device__ void fused_tail(const Solve &s, int tile, int cur, const double *sums) {
     const int T = s.T, N = s.nshift;
-    __shared__ double sh_beta[32];
-    __shared__ int sh_was_active[32];
+    __shared__ double sh_a[32], sh_b[32], sh_vrn[32], sh_rhon[32];
+    __shared__ int sh_was[32], sh_any[32];
     if (threadIdx.x < T) {
         const int t = threadIdx.x, c = tile * T + t;
-        sh_any[t] = 0;
         const int act = s.col_active[c];
-        sh_was_active[t] = act;
-        double beta = 0.0;
+        sh_was[t] = act;
+        sh_any[t] = 0;
+        double a = 0.0, b = 0.0, vrn = 0.0, rhon = 0.0;
         if (act) {
-            const double rho_new = sh_rr[t];
-            const double vr = sh_vr[t];
-            beta = rho_new / s.rho[c];
-            if (!isfinite(beta) || !isfinite(vr)) set_status(s.status, DEV_NUMERIC);
-            const double alpha = s.alpha[c];
+            const double rr = sums[0 * T + t], pw = sums[1 * T + t], rw = sums[2 * T + t];
+            const double ww = sums[3 * T + t], vr = sums[4 * T + t], vw = sums[5 * T + t];
+            if (!(pw > 0.0)) {
+                set_status(s.status, isfinite(pw) ? DEV_NOTSPD : DEV_NUMERIC);
+            } else {
+                a = rr / pw;
+                rhon = fmax(rr - 2.0 * a * rw + a * a * ww, 0.0);
+                b = rr > 0.0 ? rhon / rr : 0.0;
+                vrn = vr - a * vw;
+                if (!isfinite(a) || !isfinite(b) || !isfinite(vrn)) set_status(s.status, DEV_NUMERIC);
+            }
             // seed system (sigma = 0): pi0 = v^T x0, phi0 = v^T p
-            s.pi0[c] += alpha * s.phi0[c];
-            s.phi0[c] = vr + beta * s.phi0[c];
-            const double thr = s.tol * sqrt(s.vnorm2[c]);
-            if (sqrt(rho_new) > thr) sh_any[t] = 1;
+            s.pi0[c] += a * s.phi0[c];
+            s.phi0[c] = vrn + b * s.phi0[c];
+            s.rho[c] = rhon;
+            if (sqrt(rhon) > s.tol * sqrt(s.vnorm2[c])) sh_any[t] = 1;
         }
-        sh_beta[t] = beta;
+        sh_a[t] = a;
+        sh_b[t] = b;
+        sh_vrn[t] = vrn;
+        sh_rhon[t] = rhon;
     }
     __syncthreads();
     for (int q = threadIdx.x; q < T * N; q += blockDim.x) {
         const int t = q / N, l = q - t * N, c = tile * T + t;
-        if (!sh_was_active[t]) continue;
+        if (!sh_was[t]) continue;
         const int idx = c * N + l;
         if (!s.sh_active[idx]) continue;
-        const double alpha = s.alpha[c], beta = sh_beta[t];
+        const double alpha = sh_a[t], beta = sh_b[t];
         const double ap = s.alpha_prev[c], bp = s.beta_prev[c];
         const double2 sl = s.shift[l];
         const double2 z = s.zeta[idx], zp = s.zeta_prev[idx];
@@ -366,10 +365,10 @@ __device__ void scalar_tail(const Solve &s, int tile, const double *sh_rr, const
         const double2 bs = cscale(beta, cmul(ratio, ratio));
         const double2 phi = s.phi[idx];
         s.pi[idx] = cadd(s.pi[idx], cmul(as, phi));
-        s.phi[idx] = cadd(cscale(sh_vr[t], zn), cmul(bs, phi));
+        s.phi[idx] = cadd(cscale(sh_vrn[t], zn), cmul(bs, phi));
         s.zeta_prev[idx] = z;
         s.zeta[idx] = zn;
-        const double res = cabs2(zn) * sqrt(sh_rr[t]);
+        const double res = cabs2(zn) * sqrt(sh_rhon[t]);
         if (!isfinite(res)) set_status(s.status, DEV_NUMERIC);
         if (res > s.tol * sqrt(s.vnorm2[c])) {
             atomicOr(&sh_any[t], 1);
@@ -380,15 +379,17 @@ __device__ void scalar_tail(const Solve &s, int tile, const double *sh_rr, const
     __syncthreads();
     if (threadIdx.x < T) {
         const int t = threadIdx.x, c = tile * T + t;
-        if (sh_was_active[t]) {
-            s.alpha_prev[c] = s.alpha[c];
-            s.beta_prev[c] = sh_beta[t];
-            s.rho[c] = sh_rr[t];
+        if (sh_was[t]) {
+            s.alpha_prev[c] = sh_a[t];
+            s.beta_prev[c] = sh_b[t];
             s.col_iters[c] += 1;
             const int still = sh_any[t];
             s.col_active[c] = still;
-            s.beta[c] = still ? sh_beta[t] : 0.0;
-            if (!still) s.alpha[c] = 0.0;
+            s.alpha[c] = sh_a[t];           // applied to r and x by the next pass
+            s.beta[c] = still ? sh_b[t] : 0.0;
+        } else {
+            s.alpha[c] = 0.0;
+            s.beta[c] = 0.0;
         }
     }
     __syncthreads();
@@ -396,108 +397,107 @@ __device__ void scalar_tail(const Solve &s, int tile, const double *sh_rr, const
         int any = 0;
         for (int t = 0; t < T; ++t) any |= s.col_active[tile * T + t];
         if (!any) {
+            s.tile_par[tile] = cur ^ 1;     // set holding the final p for the x flush
             s.tile_done[tile] = 1;
             atomicSub(s.remaining, 1);
         }
     }
 }
 
-// after phase A sums: alpha_k = rho_k / p^T Q p per active column
-__device__ __forceinline__ void set_alpha(const Solve &s, int tile, int t, double pw) {
-    const int c = tile * s.T + t;
-    if (s.col_active[c]) {
-        if (!(pw > 0.0)) {
-            set_status(s.status, isfinite(pw) ? DEV_NOTSPD : DEV_NUMERIC);
-            s.alpha[c] = 0.0;
-        } else {
-            s.alpha[c] = s.rho[c] / pw;
-        }
-    } else {
-        s.alpha[c] = 0.0;
+// Per-thread dot accumulators of one pass.
+template <typename V, int T>
+struct Dots {
+    V rr[T], pw[T], rw[T], ww[T], vr[T], vw[T];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int t = 0; t < T; ++t) rr[t] = pw[t] = rw[t] = ww[t] = vr[t] = vw[t] = (V)0;
     }
-}
-
-// accumulator type: FP64 vectors accumulate in FP64; FP32 vectors accumulate each
-// thread's share in FP32 and every cross-thread sum in FP64.
-template <typename V>
-struct AccT { using type = V; };
-
-// ------------------------------------------------------------------ phase bodies
-template <typename V, int T, int KIND, bool NC>
-__device__ __forceinline__ void phaseA_points(const Solve &s, int tile, int64_t i0, int64_t stride,
-                                              const V *pold, V *pnew, double (&out)[T]) {
-    const int64_t n = s.op.n;
-    const V *r = static_cast<const V *>(s.r) + (int64_t)tile * n * T;
-    LoadRP<V, T, NC> ld;
-    ld.r = r;
-    ld.p = pold;
-#pragma unroll
-    for (int t = 0; t < T; ++t) ld.beta[t] = (V)s.beta[tile * T + t];
-    typename AccT<V>::type acc[T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) acc[t] = 0;
-    for (int64_t i = i0; i < n; i += stride) {
-        V w[T], self[T];
-        apply_row<V, T, KIND>(s.op, i, ld, w, self);
-        stpack<V, T>(pnew, i, self);
-#pragma unroll
-        for (int t = 0; t < T; ++t) acc[t] = fma(self[t], w[t], acc[t]);
-    }
-#pragma unroll
-    for (int t = 0; t < T; ++t) out[t] = (double)acc[t];
-}
-
-template <typename V, int T, int KIND, bool NC>
-__device__ __forceinline__ void phaseB_points(const Solve &s, int tile, int64_t i0, int64_t stride,
-                                              const V *pcur, double (&out)[2 * T]) {
-    const int64_t n = s.op.n;
-    V *r = static_cast<V *>(s.r) + (int64_t)tile * n * T;
-    V *x = s.keep_x0 ? static_cast<V *>(s.x) + (int64_t)tile * n * T : nullptr;
-    V alpha[T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) alpha[t] = (V)s.alpha[tile * T + t];
-    LoadP<V, T, NC> ld;
-    ld.p = pcur;
-    typename AccT<V>::type rr[T], vr[T];
-#pragma unroll
-    for (int t = 0; t < T; ++t) { rr[t] = 0; vr[t] = 0; }
-    const int cbase = tile * T;
-    for (int64_t i = i0; i < n; i += stride) {
-        V w[T], pv[T];
-        apply_row<V, T, KIND>(s.op, i, ld, w, pv);
-        Pack<V, T> rp = ldpack<V, T, false>(r, i);
-        V rn[T];
-#pragma unroll
-        for (int t = 0; t < T; ++t) rn[t] = fma(-alpha[t], w[t], rp.v[t]);
-        stpack<V, T>(r, i, rn);
-        if (x) {
-            Pack<V, T> xp = ldpack<V, T, false>(x, i);
-            V xn[T];
-#pragma unroll
-            for (int t = 0; t < T; ++t) xn[t] = fma(alpha[t], pv[t], xp.v[t]);
-            stpack<V, T>(x, i, xn);
-        }
-        const int lc = s.colour[i] - cbase;
+    // r, p, w of one vertex; lc = colour - tile base (own column if 0 <= lc < T)
+    __device__ __forceinline__ void add(const V (&r)[T], const V (&p)[T], const V (&w)[T], int lc) {
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            rr[t] = fma(rn[t], rn[t], rr[t]);
-            if (lc == t) vr[t] += rn[t];
+            rr[t] = fma(r[t], r[t], rr[t]);
+            pw[t] = fma(p[t], w[t], pw[t]);
+            rw[t] = fma(r[t], w[t], rw[t]);
+            ww[t] = fma(w[t], w[t], ww[t]);
+            if (lc == t) {
+                vr[t] += r[t];
+                vw[t] += w[t];
+            }
         }
     }
+    __device__ __forceinline__ void flat(V (&o)[NDOT * T]) const {
 #pragma unroll
-    for (int t = 0; t < T; ++t) { out[t] = (double)rr[t]; out[T + t] = (double)vr[t]; }
+        for (int t = 0; t < T; ++t) {
+            o[0 * T + t] = rr[t];
+            o[1 * T + t] = pw[t];
+            o[2 * T + t] = rw[t];
+            o[3 * T + t] = ww[t];
+            o[4 * T + t] = vr[t];
+            o[5 * T + t] = vw[t];
+        }
+    }
+};
+
+template <typename V, int T>
+__device__ __forceinline__ void load_coefs(const Solve &s, int tile, V (&a)[T], V (&b)[T]) {
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        a[t] = (V)s.alpha[tile * T + t];
+        b[t] = (V)s.beta[tile * T + t];
+    }
 }
 
-// ------------------------------------------------------------------ grid engine
-template <int K>
-__device__ __forceinline__ bool tile_last_block(const Solve &s, int tile, const double (&v)[K],
-                                                double *part_base) {
-    // thread 0 holds the block sums: publish them, count the block in.
-    __shared__ int is_last;
-    if (threadIdx.x == 0) {
+// Generic pass body over vertices i0, i0+stride, ... (any kind; stencil taps
+// gathered through the loader).  NC: read-only cache path allowed.
+template <typename V, int T, int KIND, bool NC>
+__device__ __forceinline__ void pass_points(const Solve &s, int tile, int cur, int64_t i0,
+                                            int64_t stride, Dots<V, T> &d) {
+    const int64_t n = s.op.n;
+    const int64_t off = (int64_t)tile * n * T;
+    const V *r = static_cast<const V *>(s.rbuf[cur]) + off;
+    const V *w = static_cast<const V *>(s.wbuf[cur]) + off;
+    const V *p = static_cast<const V *>(s.pbuf[cur]) + off;
+    V *rn = static_cast<V *>(s.rbuf[cur ^ 1]) + off;
+    V *wn = static_cast<V *>(s.wbuf[cur ^ 1]) + off;
+    V *pn = static_cast<V *>(s.pbuf[cur ^ 1]) + off;
+    V *x = s.keep_x0 ? static_cast<V *>(s.x) + off : nullptr;
+    LoadFused<V, T, NC> ld;
+    ld.r = r;
+    ld.w = w;
+    ld.p = p;
+    load_coefs<V, T>(s, tile, ld.a, ld.b);
+    const int cbase = tile * T;
+    for (int64_t i = i0; i < n; i += stride) {
+        V wv[T], pv[T];
+        apply_row<V, T, KIND>(s.op, i, ld, wv, pv);
+        const Pack<V, T> ri = ldpack<V, T, NC>(r, i), wi = ldpack<V, T, NC>(w, i);
+        V rv[T];
 #pragma unroll
-        for (int k = 0; k < K; ++k) part_base[k] = v[k];
-        __threadfence();
+        for (int t = 0; t < T; ++t) rv[t] = fma(-ld.a[t], wi.v[t], ri.v[t]);
+        stpack<V, T>(rn, i, rv);
+        stpack<V, T>(pn, i, pv);
+        stpack<V, T>(wn, i, wv);
+        if (x) {
+            const Pack<V, T> po = ldpack<V, T, NC>(p, i);
+            Pack<V, T> xo = ldpack<V, T, false>(x, i);
+            V xv[T];
+#pragma unroll
+            for (int t = 0; t < T; ++t) xv[t] = fma(ld.a[t], po.v[t], xo.v[t]);
+            stpack<V, T>(x, i, xv);
+        }
+        d.add(rv, pv, wv, s.colour[i] - cbase);
+    }
+}
+
+// ------------------------------------------------------------------ grid engine (generic)
+// The last CTA of a tile to finish reduces the tile's partials (fixed order)
+// and runs the tail.  Returns true in that CTA.
+__device__ __forceinline__ bool tile_last_block(const Solve &s, int tile) {
+    __shared__ int is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
         const int prev = atomicAdd(&s.tile_ctr[tile], 1);
         is_last = (prev == (int)gridDim.x - 1);
     }
@@ -506,106 +506,413 @@ __device__ __forceinline__ bool tile_last_block(const Solve &s, int tile, const 
     return is_last;
 }
 
-template <typename V, int T, int KIND>
-__global__ void __launch_bounds__(256) k_phaseA(Solve s, int parity) {
-    const int tile = blockIdx.y;
-    if (s.tile_done[tile]) return;
-    const int64_t off = (int64_t)tile * s.op.n * T;
-    const V *pold = static_cast<const V *>(parity ? s.p1 : s.p0) + off;
-    V *pnew = static_cast<V *>(parity ? s.p0 : s.p1) + off;
-    double v[T];
-    phaseA_points<V, T, KIND, true>(s, tile, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                                    (int64_t)gridDim.x * blockDim.x, pold, pnew, v);
-    __shared__ double red[32 * T];
-    block_sum<T>(v, red);
-    double *part = s.partial + ((int64_t)tile * s.bpt + blockIdx.x) * T * 2;
-    if (tile_last_block<T>(s, tile, v, part)) {
-        if (threadIdx.x < T) {
-            double pw = 0.0;
-            for (int b = 0; b < (int)gridDim.x; ++b)
-                pw += s.partial[((int64_t)tile * s.bpt + b) * T * 2 + threadIdx.x];
-            set_alpha(s, tile, threadIdx.x, pw);
-        }
-        if (threadIdx.x == 0) s.tile_ctr[tile] = 0;
+// Block sum of K per-thread values into out[K] (shared memory): warp shuffle
+// trees, then threads k < K add the per-warp sums in a fixed order.  red needs
+// (blockDim/32)*K doubles.  Deterministic for a fixed launch shape.
+template <typename A, int K>
+__device__ __forceinline__ void block_sum_to(const A (&v)[K], double *red, double *out) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double x = (double)v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[wid * K + k] = x;
     }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        double acc = 0.0;
+        for (int w = 0; w < nw; ++w) acc += red[w * K + k];
+        out[k] = acc;
+    }
+    __syncthreads();
+}
+
+// Publish this CTA's K sums (cta[], shared memory) as its partial; in the tile's
+// last CTA add all partials in a fixed order (chunks of CTAs per thread group,
+// then the chunk sums) and run the tail.  scratch: >= blockDim.x doubles.
+// Called by every thread of every (non-skipped) CTA of the grid engine.
+template <int K>
+__device__ __forceinline__ void publish_and_tail(const Solve &s, int tile, int cur,
+                                                 const double *cta, double *scratch) {
+    __shared__ double sums[K];
+    double *part = s.partial + ((int64_t)tile * s.bpt + blockIdx.x) * K;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) part[k] = cta[k];
+    if (!tile_last_block(s, tile)) return;
+    const int chunks = blockDim.x / K;          // >= 1 (K <= 48 < blockDim.x)
+    const int nb = (int)gridDim.x;
+    const int per = (nb + chunks - 1) / chunks;
+    if (threadIdx.x < chunks * K) {
+        const int k = threadIdx.x % K, ch = threadIdx.x / K;
+        double acc = 0.0;
+        const int b1 = min(nb, (ch + 1) * per);
+        for (int b = ch * per; b < b1; ++b) acc += s.partial[((int64_t)tile * s.bpt + b) * K + k];
+        scratch[ch * K + k] = acc;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        double acc = 0.0;
+        for (int ch = 0; ch < chunks; ++ch) acc += scratch[ch * K + k];
+        sums[k] = acc;
+    }
+    __syncthreads();
+    fused_tail(s, tile, cur, sums);
+    if (threadIdx.x == 0) s.tile_ctr[tile] = 0;
+}
+
+template <typename V, int T>
+__device__ __forceinline__ void finish_pass(const Solve &s, int tile, int cur, const Dots<V, T> &d) {
+    constexpr int K = NDOT * T;
+    __shared__ double red[32 * K];
+    __shared__ double cta[K];
+    V flat[K];
+    d.flat(flat);
+    block_sum_to<V, K>(flat, red, cta);
+    publish_and_tail<K>(s, tile, cur, cta, red);
 }
 
 template <typename V, int T, int KIND>
-__global__ void __launch_bounds__(256) k_phaseB(Solve s, int parity) {
+__global__ void __launch_bounds__(256) k_pass(Solve s, int cur) {
     const int tile = blockIdx.y;
     if (s.tile_done[tile]) return;
-    const int64_t off = (int64_t)tile * s.op.n * T;
-    const V *pcur = static_cast<const V *>(parity ? s.p0 : s.p1) + off;
-    double v[2 * T];
-    phaseB_points<V, T, KIND, true>(s, tile, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                                    (int64_t)gridDim.x * blockDim.x, pcur, v);
-    __shared__ double red[32 * 2 * T];
-    block_sum<2 * T>(v, red);
-    double *part = s.partial + ((int64_t)tile * s.bpt + blockIdx.x) * T * 2;
-    if (tile_last_block<2 * T>(s, tile, v, part)) {
-        __shared__ double sh_rr[T], sh_vr[T];
-        __shared__ int sh_any[T];
-        if (threadIdx.x < T) {
-            double a = 0.0, b = 0.0;
-            for (int bl = 0; bl < (int)gridDim.x; ++bl) {
-                const double *q = s.partial + ((int64_t)tile * s.bpt + bl) * T * 2;
-                a += q[threadIdx.x];
-                b += q[T + threadIdx.x];
-            }
-            sh_rr[threadIdx.x] = a;
-            sh_vr[threadIdx.x] = b;
-        }
-        __syncthreads();
-        scalar_tail(s, tile, sh_rr, sh_vr, sh_any);
-        if (threadIdx.x == 0) s.tile_ctr[tile] = 0;
+    Dots<V, T> d;
+    d.zero();
+    pass_points<V, T, KIND, true>(s, tile, cur, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                                  (int64_t)gridDim.x * blockDim.x, d);
+    finish_pass<V, T>(s, tile, cur, d);
+}
+
+// ------------------------------------------------------------------ streaming 2D grid engine
+// For the 2D lattice kinds a CTA owns a strip of SW = 128 lattice columns
+// (an H-wide halo on each side, H = 1 for the 5-point Q and 2 for the
+// 13-point square) and a segment of rows, and marches down the rows.  G
+// threads share one lattice column, each holding TS = T/G probing columns.
+// Per row step a thread
+//   forms p_k and r_k at (x, y) from r, w, p of the previous set (loads issued
+//     two rows ahead into registers),
+//   [13-point] forms u = Q1 p at (x, y-1),
+//   forms w = Q p at (x, y-H) and writes r_k, p_k, w_k there,
+// where vertical neighbours come from the thread's own register window and
+// horizontal neighbours from two double-buffered shared-memory rows: one
+// barrier per row, about six shared-memory accesses per vertex and column
+// pack.  Out-of-grid rows and columns are zero, the Dirichlet ghost values of
+// the difference form
+//   (kappa2 I - Lap) p at i = kappa2 p_i + sum_{4 neighbours j} (p_i - p_j);
+// a torus wraps its indices.  The 13-point square applies that form twice.
+constexpr int SW = 128;
+
+template <int KIND>
+struct Strip {
+    static constexpr int H = KIND == KIND_2D13_SQ ? 2 : 1;
+    static constexpr int W = SW - 2 * H;   // output columns per strip
+};
+
+// threads per lattice column: one thread holds all T columns of its lattice
+// column, so per-row address, loop and barrier work is shared by T columns
+template <typename V, int T>
+constexpr int stream_groups() {
+    return 1;
+}
+
+__device__ __forceinline__ int wrap_coord(int g, int n, bool per, bool &in) {
+    if (g >= 0 && g < n) {
+        in = true;
+        return g;
     }
+    if (!per) {
+        in = false;
+        return 0;
+    }
+    in = true;
+    g %= n;
+    return g < 0 ? g + n : g;
+}
+
+// asynchronous global -> shared copy of one pack (16- or 8-byte pieces); src-size 0
+// zero-fills
+template <typename V, int TS>
+__device__ __forceinline__ void cp_async_pack(Pack<V, TS> *dst, const V *src, bool valid) {
+    constexpr int BYTES = sizeof(V) * TS;
+    static_assert(BYTES % 8 == 0, "packs are a multiple of 8 bytes");
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const char *g = reinterpret_cast<const char *>(src);
+    if constexpr (BYTES % 16 == 0) {
+#pragma unroll
+        for (int k = 0; k < BYTES / 16; ++k)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d + 16 * k),
+                         "l"(g + 16 * k), "r"(valid ? 16 : 0));
+    } else {
+#pragma unroll
+        for (int k = 0; k < BYTES / 8; ++k)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d + 8 * k),
+                         "l"(g + 8 * k), "r"(valid ? 8 : 0));
+    }
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+template <typename V, int TS>
+__device__ __forceinline__ Pack<V, TS> zero_pack() {
+    Pack<V, TS> z;
+#pragma unroll
+    for (int t = 0; t < TS; ++t) z.v[t] = (V)0;
+    return z;
+}
+
+// (c p + sum of the four differences), the difference-form stencil of one level
+template <typename V, int TS>
+__device__ __forceinline__ Pack<V, TS> diff5(V c, const Pack<V, TS> &pc, const Pack<V, TS> &pl,
+                                             const Pack<V, TS> &pr, const Pack<V, TS> &pd,
+                                             const Pack<V, TS> &pu) {
+    Pack<V, TS> o;
+#pragma unroll
+    for (int t = 0; t < TS; ++t)
+        o.v[t] = fma(c, pc.v[t], ((pc.v[t] - pl.v[t]) + (pc.v[t] - pr.v[t])) +
+                                     ((pc.v[t] - pd.v[t]) + (pc.v[t] - pu.v[t])));
+    return o;
+}
+
+// resident CTAs per SM the register budget is sized for
+constexpr int stream_min_blocks(int G) { return G == 1 ? 3 : 2; }
+template <typename V, int T>
+constexpr int stream_min_blocks_t() { return sizeof(V) * T <= 8 ? 6 : (sizeof(V) * T <= 16 ? 4 : 3); }
+
+constexpr int STREAM_PD = 6;   // ring depth: rows held per thread (cp.async)
+
+template <typename V, int T, int G>
+constexpr size_t stream_smem_bytes() {
+    constexpr int TS = T / G;
+    constexpr size_t pk = sizeof(Pack<V, TS>);
+    constexpr size_t rows = (4 + 3 * STREAM_PD) * SW * G * pk + STREAM_PD * SW * G * sizeof(int);
+    constexpr size_t part = (size_t)SW * G * NDOT * TS * sizeof(V);
+    constexpr size_t red = (size_t)SW * G * sizeof(double);
+    return rows > part ? (rows > red ? rows : red) : (part > red ? part : red);
+}
+
+template <typename V, int T, int G, int KIND, bool KEEPX>
+__global__ void __launch_bounds__(SW * G, stream_min_blocks_t<V, T>()) k_stream2d(Solve s, int cur) {
+    constexpr int TS = T / G, H = Strip<KIND>::H, K = NDOT * T, PD = STREAM_PD;
+    constexpr int NT = SW * G;          // threads; also the pack count of one shared row
+    using P = Pack<V, TS>;
+    const int tile = blockIdx.y;
+    if (s.tile_done[tile]) return;
+    // shared: [ps: 2 rows | us: 2 rows | ring: PD x (r, w, p) rows]; the ring is
+    // per-thread private (each thread copies and reads back only its own packs), so
+    // it needs no barrier.  After the row loop the bytes hold the partial sums.
+    extern __shared__ __align__(16) unsigned char smem[];
+    P *const ps = reinterpret_cast<P *>(smem);
+    P *const us = ps + 2 * NT;
+    P *const ring = ps + 4 * NT + threadIdx.x;
+    int *const ringc = reinterpret_cast<int *>(ps + (4 + 3 * PD) * NT) + threadIdx.x;
+    const int nx = s.op.nx, ny = s.op.ny;
+    const bool per = s.op.periodic;
+    const int xl = threadIdx.x / G, g = threadIdx.x - xl * G;
+    const int strip = blockIdx.x % s.strips, sg = blockIdx.x / s.strips;
+    const int gx = strip * Strip<KIND>::W - H + xl;
+    bool inx;
+    const int gxw = wrap_coord(gx, nx, per, inx);
+    const bool outx = xl >= H && xl < H + Strip<KIND>::W && gx < nx;
+    const int ys = sg * s.seg, ye = min(ys + s.seg, ny);
+    const int cb = tile * T + g * TS;
+    const int64_t off = (int64_t)tile * s.op.n * T + g * TS;
+    const V *const r = static_cast<const V *>(cur ? s.rbuf[1] : s.rbuf[0]) + off;
+    const V *const w = static_cast<const V *>(cur ? s.wbuf[1] : s.wbuf[0]) + off;
+    const V *const p = static_cast<const V *>(cur ? s.pbuf[1] : s.pbuf[0]) + off;
+    V a[TS], b[TS];
+    V d_rr[TS], d_pw[TS], d_rw[TS], d_ww[TS], d_vr[TS], d_vw[TS];
+#pragma unroll
+    for (int t = 0; t < TS; ++t) {
+        a[t] = (V)s.alpha[cb + t];
+        b[t] = (V)s.beta[cb + t];
+        d_rr[t] = d_pw[t] = d_rw[t] = d_ww[t] = d_vr[t] = d_vw[t] = (V)0;
+    }
+    P pw0 = zero_pack<V, TS>(), pw1 = pw0, pw2 = pw0;   // p at rows y-2, y-1, y
+    P uw0 = pw0, uw1 = pw0, uw2 = pw0;                   // u at rows y-3, y-2, y-1
+
+    int y = ys - H;
+    const int yend = ye + H;
+    // rows past the segment's last step are not needed: empty (zero-fill) group
+    auto load_row = [&](int yr, int slot) {
+        bool iny;
+        const int gyw = wrap_coord(yr, ny, per, iny);
+        const bool in = iny && inx && yr < yend;
+        const int64_t e = in ? ((int64_t)gyw * nx + gxw) * T : 0;
+        P *q = ring + slot * 3 * NT;
+        cp_async_pack<V, TS>(q, r + e, in);
+        cp_async_pack<V, TS>(q + NT, w + e, in);
+        cp_async_pack<V, TS>(q + 2 * NT, p + e, in);
+        {
+            const unsigned dc = (unsigned)__cvta_generic_to_shared(ringc + slot * NT);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dc),
+                         "l"(s.colour + (in ? (int64_t)gyw * nx + gxw : 0)), "r"(in ? 4 : 0));
+        }
+        cp_async_commit();
+    };
+    // outputs at (gx, y) of lattice row y held in ring slot `slot`
+    auto emit = [&](int y, int slot, const P &pk, const P &wk) {
+        const P *q = ring + slot * 3 * NT;
+        const P r0 = q[0], w0 = q[NT];
+        P rk;
+#pragma unroll
+        for (int t = 0; t < TS; ++t) rk.v[t] = fma(-a[t], w0.v[t], r0.v[t]);
+        const int64_t gi = (int64_t)y * nx + gx;
+        const int64_t e = gi * T;
+        V *rn = static_cast<V *>(cur ? s.rbuf[0] : s.rbuf[1]) + off;
+        V *wn = static_cast<V *>(cur ? s.wbuf[0] : s.wbuf[1]) + off;
+        V *pn = static_cast<V *>(cur ? s.pbuf[0] : s.pbuf[1]) + off;
+        *reinterpret_cast<P *>(rn + e) = rk;
+        *reinterpret_cast<P *>(pn + e) = pk;
+        *reinterpret_cast<P *>(wn + e) = wk;
+        if constexpr (KEEPX) {
+            V *x = static_cast<V *>(s.x) + off;
+            const P p0 = q[2 * NT];
+            P xo = *reinterpret_cast<const P *>(x + e);
+#pragma unroll
+            for (int t = 0; t < TS; ++t) xo.v[t] = fma(a[t], p0.v[t], xo.v[t]);
+            *reinterpret_cast<P *>(x + e) = xo;
+        }
+        const int lc = ringc[slot * NT] - cb;
+#pragma unroll
+        for (int t = 0; t < TS; ++t) {
+            d_rr[t] = fma(rk.v[t], rk.v[t], d_rr[t]);
+            d_pw[t] = fma(pk.v[t], wk.v[t], d_pw[t]);
+            d_rw[t] = fma(rk.v[t], wk.v[t], d_rw[t]);
+            d_ww[t] = fma(wk.v[t], wk.v[t], d_ww[t]);
+            if (lc == t) {
+                d_vr[t] += rk.v[t];
+                d_vw[t] += wk.v[t];
+            }
+        }
+    };
+
+    // ring slot of row yr is (yr - y0) mod PD.  A row is live from its p-step to its
+    // emit step H rows later; at the end of step y the slot of row y - H takes row
+    // y - H + PD, so the prologue queues rows y0 .. y0 + PD - H - 1 and row y's
+    // copy group is always the (y - y0 + 1)-th: waiting with PD - H - 1 groups
+    // pending completes it.
+#pragma unroll
+    for (int k = 0; k < PD - H; ++k) load_row(y + k, k);
+    int slot = 0;            // slot of row y
+    for (; y < yend; ++y) {
+        cp_async_wait<PD - 1 - H>();
+        {
+            const P *q = ring + slot * 3 * NT;
+            const P r0 = q[0], w0 = q[NT], p0 = q[2 * NT];
+            P pk;
+#pragma unroll
+            for (int t = 0; t < TS; ++t) pk.v[t] = fma(b[t], p0.v[t], fma(-a[t], w0.v[t], r0.v[t]));
+            ps[(y & 1) * NT + threadIdx.x] = pk;
+            pw0 = pw1;
+            pw1 = pw2;
+            pw2 = pk;
+        }
+        const int slot_h = slot - H < 0 ? slot - H + PD : slot - H;   // slot of row y - H
+        const V sc = (V)s.op.scale;
+        if constexpr (KIND == KIND_2D13_SQ) {
+            const V k2 = (V)s.op.kappa2;
+            // u = Q1 p at (x, y-1): p row y-1 was shared last step
+            if (y >= ys) {
+                P u = zero_pack<V, TS>();
+                bool uin;
+                wrap_coord(y - 1, ny, per, uin);
+                if (uin && inx && xl >= 1 && xl < SW - 1) {
+                    const P *row = ps + ((y - 1) & 1) * NT;
+                    u = diff5<V, TS>(k2, pw1, row[threadIdx.x - G], row[threadIdx.x + G], pw0, pw2);
+                }
+                us[((y - 1) & 1) * NT + threadIdx.x] = u;
+                uw0 = uw1;
+                uw1 = uw2;
+                uw2 = u;
+            }
+            // w = Q1 u at (x, y-2): u row y-2 was shared last step
+            if (y - 2 >= ys && y - 2 < ye && outx) {
+                const P *row = us + ((y - 2) & 1) * NT;
+                P wk = diff5<V, TS>(k2, uw1, row[threadIdx.x - G], row[threadIdx.x + G], uw0, uw2);
+#pragma unroll
+                for (int t = 0; t < TS; ++t) wk.v[t] *= sc;
+                emit(y - 2, slot_h, pw0, wk);
+            }
+        } else {
+            // w = Q p at (x, y-1): p row y-1 was shared last step
+            if (y - 1 >= ys && y - 1 < ye && outx) {
+                const int64_t gi = (int64_t)(y - 1) * nx + gx;
+                V dg = field_at<V>(s.op, gi);
+                if (s.op.mask) dg += (V)s.op.tau * (V)s.op.mask[gi];
+                const P *row = ps + ((y - 1) & 1) * NT;
+                P wk = diff5<V, TS>(dg, pw1, row[threadIdx.x - G], row[threadIdx.x + G], pw0, pw2);
+#pragma unroll
+                for (int t = 0; t < TS; ++t) wk.v[t] *= sc;
+                emit(y - 1, slot_h, pw1, wk);
+            }
+        }
+        // row y - H is done: its slot takes row y - H + PD
+        load_row(y - H + PD, slot_h);
+        slot = slot + 1 == PD ? 0 : slot + 1;
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+    // CTA sums: per-thread partials -> shared, then one thread per (dot, column)
+    // adds the partials of its SW lattice columns in a fixed order (FP64)
+    V *part = reinterpret_cast<V *>(smem);
+    {
+        V *mine = part + threadIdx.x * NDOT * TS;
+#pragma unroll
+        for (int t = 0; t < TS; ++t) {
+            mine[0 * TS + t] = d_rr[t];
+            mine[1 * TS + t] = d_pw[t];
+            mine[2 * TS + t] = d_rw[t];
+            mine[3 * TS + t] = d_ww[t];
+            mine[4 * TS + t] = d_vr[t];
+            mine[5 * TS + t] = d_vw[t];
+        }
+    }
+    __syncthreads();
+    __shared__ double cta[K];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        const int dot = k / T, col = k - dot * T;
+        const int gg = col / TS, t = col - gg * TS;
+        double acc = 0.0;
+        for (int xx = 0; xx < SW; ++xx) acc += (double)part[(xx * G + gg) * NDOT * TS + dot * TS + t];
+        cta[k] = acc;
+    }
+    __syncthreads();
+    publish_and_tail<K>(s, tile, cur, cta, reinterpret_cast<double *>(smem));
 }
 
 // ------------------------------------------------------------------ CTA engine
+// One CTA runs a tile's whole solve (small problems): the same fused pass,
+// block barriers only, sets alternating inside the kernel (coherent loads).
 template <typename V, int T, int KIND>
-__global__ void __launch_bounds__(512) k_cta_solve(Solve s, int max_iter) {
+__global__ void __launch_bounds__(256) k_cta_solve(Solve s, int max_iter) {
+    constexpr int K = NDOT * T;
     const int tile = blockIdx.x;
-    const int64_t off = (int64_t)tile * s.op.n * T;
-    __shared__ double red[32 * 2 * T];
-    __shared__ double sh_rr[T], sh_vr[T];
-    __shared__ int sh_any[T];
+    __shared__ double red[8 * K];
+    __shared__ double sums[K];
     __shared__ int done;
     if (threadIdx.x == 0) done = s.tile_done[tile];
     __syncthreads();
     for (int it = 0; it < max_iter && !done; ++it) {
-        const int parity = it & 1;
-        const V *pold = static_cast<const V *>(parity ? s.p1 : s.p0) + off;
-        V *pnew = static_cast<V *>(parity ? s.p0 : s.p1) + off;
-        double va[T];
-        phaseA_points<V, T, KIND, false>(s, tile, threadIdx.x, blockDim.x, pold, pnew, va);
-        block_sum<T>(va, red);
-        if (threadIdx.x == 0) {
-            for (int t = 0; t < T; ++t) red[t] = va[t];
-        }
-        __syncthreads();
-        if (threadIdx.x < T) set_alpha(s, tile, threadIdx.x, red[threadIdx.x]);
-        __syncthreads();
-        double vb[2 * T];
-        phaseB_points<V, T, KIND, false>(s, tile, threadIdx.x, blockDim.x, pnew, vb);
-        block_sum<2 * T>(vb, red);
-        if (threadIdx.x == 0) {
-            for (int t = 0; t < T; ++t) { sh_rr[t] = vb[t]; sh_vr[t] = vb[T + t]; }
-        }
-        __syncthreads();
-        scalar_tail(s, tile, sh_rr, sh_vr, sh_any);
+        const int cur = it & 1;
+        Dots<V, T> d;
+        d.zero();
+        pass_points<V, T, KIND, false>(s, tile, cur, threadIdx.x, blockDim.x, d);
+        V flat[K];
+        d.flat(flat);
+        block_sum_to<V, K>(flat, red, sums);
+        fused_tail(s, tile, cur, sums);
         __syncthreads();
         if (threadIdx.x == 0) done = s.tile_done[tile] || (*s.status != 0);
         __syncthreads();
     }
 }
 
-// ------------------------------------------------------------------ init / finish
+// ------------------------------------------------------------------ init / flush / finish
 template <typename V, int T>
 __global__ void k_init_vectors(Solve s) {
     const int64_t n = s.op.n;
     const int64_t total = (int64_t)s.ntiles * n;
-    V *r = static_cast<V *>(s.r), *p0 = static_cast<V *>(s.p0), *p1 = static_cast<V *>(s.p1);
-    V *x = s.keep_x0 ? static_cast<V *>(s.x) : nullptr;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
          q += (int64_t)gridDim.x * blockDim.x) {
         const int tile = (int)(q / n);
@@ -618,10 +925,29 @@ __global__ void k_init_vectors(Solve s) {
             a[t] = (lc == t && s.col_active[c]) ? (V)1 : (V)0;
             z[t] = (V)0;
         }
-        stpack<V, T>(r, q, a);
-        stpack<V, T>(p0, q, z);
-        stpack<V, T>(p1, q, z);
-        if (x) stpack<V, T>(x, q, z);
+        stpack<V, T>(static_cast<V *>(s.rbuf[0]), q, a);
+        stpack<V, T>(static_cast<V *>(s.wbuf[0]), q, z);
+        stpack<V, T>(static_cast<V *>(s.pbuf[0]), q, z);
+        if (s.keep_x0) stpack<V, T>(static_cast<V *>(s.x), q, z);
+    }
+}
+
+// the final x += alpha_J p_J of each tile (its last pass J wrote p_J to set tile_par)
+template <typename V, int T>
+__global__ void k_flush_x(Solve s) {
+    const int64_t n = s.op.n;
+    const int64_t total = (int64_t)s.ntiles * n;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int tile = (int)(q / n);
+        if (!s.tile_done[tile]) continue;
+        const V *p = static_cast<const V *>(s.pbuf[s.tile_par[tile]]);
+        V *x = static_cast<V *>(s.x);
+        const Pack<V, T> pp = ldpack<V, T, false>(p, q);
+        Pack<V, T> xo = ldpack<V, T, false>(x, q);
+#pragma unroll
+        for (int t = 0; t < T; ++t) xo.v[t] = fma((V)s.alpha[tile * T + t], pp.v[t], xo.v[t]);
+        *reinterpret_cast<Pack<V, T> *>(x + q * T) = xo;
     }
 }
 
@@ -651,8 +977,10 @@ __global__ void k_init_scalars(Solve s, int col_begin, int col_end, const double
         s.col_active[c] = act;
         s.col_iters[c] = 0;
     }
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < s.ntiles; t += gridDim.x * blockDim.x)
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < s.ntiles; t += gridDim.x * blockDim.x) {
         s.tile_ctr[t] = 0;
+        s.tile_par[t] = 0;
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) *s.status = 0;
 }
 
@@ -671,7 +999,7 @@ __global__ void k_init_tiles(Solve s) {
     if (threadIdx.x == 0) *s.remaining = cnt;
 }
 
-// terms[c] = Re sum_l alpha_l pi_{c,l}; result = sum over [cb, ce) in column order.
+// terms[c] = Re sum_l alpha_l pi_{c,l}; result = sums over [cb, ce) in column order.
 __global__ void k_finish(Solve s, int cb, int ce) {
     const int N = s.nshift;
     for (int c = threadIdx.x; c < s.ncols; c += blockDim.x) {
@@ -800,9 +1128,10 @@ __global__ void k_grad(Solve s, int nparam, int p0, int p1, int p2, double *part
          i += (int64_t)gridDim.x * blockDim.x)
         for (int k = 0; k < nparam; ++k) acc[k] += grad_row<V>(s, pid[k], i);
     __shared__ double red[32 * 3];
-    block_sum<3>(acc, red);
+    __shared__ double tot[3];
+    block_sum_to<double, 3>(acc, red, tot);
     if (threadIdx.x == 0)
-        for (int k = 0; k < 3; ++k) part[blockIdx.x * 3 + k] = acc[k];
+        for (int k = 0; k < 3; ++k) part[blockIdx.x * 3 + k] = tot[k];
 }
 
 __global__ void k_grad_finish(int nblocks, const double *part, double *out) {
@@ -831,12 +1160,14 @@ static int dispatch(int precision, int T, int kind, A &&...args) {
         switch (T) {
             case 1: return dispatch_kind<double, 1, Launcher>(kind, args...);
             case 2: return dispatch_kind<double, 2, Launcher>(kind, args...);
+            case 3: return dispatch_kind<double, 3, Launcher>(kind, args...);
             case 4: return dispatch_kind<double, 4, Launcher>(kind, args...);
         }
     } else {
         switch (T) {
             case 2: return dispatch_kind<float, 2, Launcher>(kind, args...);
             case 4: return dispatch_kind<float, 4, Launcher>(kind, args...);
+            case 6: return dispatch_kind<float, 6, Launcher>(kind, args...);
             case 8: return dispatch_kind<float, 8, Launcher>(kind, args...);
         }
     }
@@ -845,10 +1176,17 @@ static int dispatch(int precision, int T, int kind, A &&...args) {
 
 template <typename V, int T, int KIND>
 struct IterLauncher {
-    static int run(const Solve &s, int parity, cudaStream_t st) {
+    static int run(const Solve &s, int cur, cudaStream_t st) {
         dim3 grid(s.bpt, s.ntiles);
-        k_phaseA<V, T, KIND><<<grid, 256, 0, st>>>(s, parity);
-        k_phaseB<V, T, KIND><<<grid, 256, 0, st>>>(s, parity);
+        if constexpr (KIND == KIND_2D5 || KIND == KIND_2D13_SQ) {
+            constexpr int G = stream_groups<V, T>();
+            if (s.keep_x0)
+                k_stream2d<V, T, G, KIND, true><<<grid, SW * G, stream_smem_bytes<V, T, G>(), st>>>(s, cur);
+            else
+                k_stream2d<V, T, G, KIND, false><<<grid, SW * G, stream_smem_bytes<V, T, G>(), st>>>(s, cur);
+        } else {
+            k_pass<V, T, KIND><<<grid, 256, 0, st>>>(s, cur);
+        }
         return (int)cudaGetLastError();
     }
 };
@@ -856,7 +1194,19 @@ struct IterLauncher {
 template <typename V, int T, int KIND>
 struct CtaLauncher {
     static int run(const Solve &s, int max_iter, cudaStream_t st) {
-        k_cta_solve<V, T, KIND><<<s.ntiles, 512, 0, st>>>(s, max_iter);
+        k_cta_solve<V, T, KIND><<<s.ntiles, 256, 0, st>>>(s, max_iter);
+        return (int)cudaGetLastError();
+    }
+};
+
+template <typename V, int T, int KIND>
+struct FlushLauncher {
+    static int run(const Solve &s, cudaStream_t st) {
+        const int64_t total = (int64_t)s.ntiles * s.op.n;
+        int blocks = (int)((total + 255) / 256);
+        if (blocks > 152 * 16) blocks = 152 * 16;
+        if (blocks < 1) blocks = 1;
+        k_flush_x<V, T><<<blocks, 256, 0, st>>>(s);
         return (int)cudaGetLastError();
     }
 };
@@ -886,13 +1236,54 @@ struct ApplyLauncher {
     }
 };
 
-int engine_blocks_per_tile(const Solve &s) {
-    const int64_t target = 152 * 8;   // one resident wave of 256-thread CTAs
-    int64_t bpt = (target + s.ntiles - 1) / s.ntiles;
+template <typename V, int T, int KIND>
+struct OccLauncher {
+    // resident CTAs per SM of the iteration kernels (the smaller of the two phases)
+    static int run(int *out) {
+        int a = 0, b = 0;
+        if constexpr (KIND == KIND_2D5 || KIND == KIND_2D13_SQ) {
+            constexpr int G = stream_groups<V, T>();
+            constexpr size_t sm = stream_smem_bytes<V, T, G>();
+            if (cudaFuncSetAttribute(k_stream2d<V, T, G, KIND, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+                cudaFuncSetAttribute(k_stream2d<V, T, G, KIND, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+                return (int)cudaGetLastError();
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_stream2d<V, T, G, KIND, true>, SW * G, sm);
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pass<V, T, KIND>, 256, 0);
+        }
+        (void)b;
+        *out = a;
+        return (int)cudaGetLastError();
+    }
+};
+
+int engine_plan(Solve &s) {
+    int dev = 0, sms = 152, occ = 8;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (dispatch<OccLauncher>(s.precision, s.T, s.op.kind, &occ) != 0 || occ < 1) occ = 1;
+    const int64_t target = (int64_t)sms * occ;   // exactly one resident wave
+    s.strips = 1;
+    s.seg = 1;
+    if (s.op.kind == KIND_2D5 || s.op.kind == KIND_2D13_SQ) {
+        const int W = s.op.kind == KIND_2D13_SQ ? Strip<KIND_2D13_SQ>::W : Strip<KIND_2D5>::W;
+        s.strips = (s.op.nx + W - 1) / W;
+        int64_t nsegs = target / ((int64_t)s.strips * s.ntiles);
+        if (nsegs < 1) nsegs = 1;
+        if (nsegs > s.op.ny) nsegs = s.op.ny;
+        s.seg = (int)((s.op.ny + nsegs - 1) / nsegs);
+        nsegs = (s.op.ny + s.seg - 1) / s.seg;
+        s.bpt = (int)(s.strips * nsegs);
+        return s.bpt;
+    }
+    int64_t bpt = target / s.ntiles;
     const int64_t need = (s.op.n + 255) / 256;
     if (bpt > need) bpt = need;
     if (bpt < 1) bpt = 1;
-    return (int)bpt;
+    s.bpt = (int)bpt;
+    return s.bpt;
 }
 
 int engine_init(const Solve &s, int col_begin, int col_end, void *stream) {
@@ -914,6 +1305,10 @@ int engine_iteration(const Solve &s, int parity, void *stream) {
 int engine_cta_solve(const Solve &s, int max_iter, void *stream) {
     return dispatch<CtaLauncher>(s.precision, s.T, s.op.kind, s, max_iter,
                                  static_cast<cudaStream_t>(stream));
+}
+
+int engine_flush_x(const Solve &s, void *stream) {
+    return dispatch<FlushLauncher>(s.precision, s.T, s.op.kind, s, static_cast<cudaStream_t>(stream));
 }
 
 int engine_finish(const Solve &s, int col_begin, int col_end, void *stream) {

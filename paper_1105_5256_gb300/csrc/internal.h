@@ -54,12 +54,16 @@ struct Solve {
     int ntiles;
     int ncols;             // padded columns = ntiles * T
     int nshift;            // N
-    int bpt;               // blocks per tile (grid engine)
+    int bpt;               // CTAs per tile (grid engine)
+    int strips, seg;       // 2D kinds: lattice strips per tile, rows per CTA segment
     int precision;         // 0 fp64, 1 mixed
     int keep_x0;
     double tol;
     const int32_t *colour; // n
-    void *r, *p0, *p1, *x; // [ntiles][n][T] in the vector precision
+    // CG state, two sets read/written alternately by consecutive passes:
+    // set[k & 1] -> set[(k & 1) ^ 1]; each [ntiles][n][T] in the vector precision
+    void *rbuf[2], *wbuf[2], *pbuf[2];
+    void *x;               // seed solution (gradient mode)
     // per-column scalars (ncols)
     double *rho, *alpha, *beta, *alpha_prev, *beta_prev, *vnorm2, *pi0, *phi0;
     int32_t *col_active, *col_iters;
@@ -69,24 +73,28 @@ struct Solve {
     const double2 *shift;  // s_l = -sigma_l
     const double2 *weight; // alpha_l
     // per tile
-    int32_t *tile_done, *tile_ctr;
-    double *partial;       // [ntiles][bpt][T][2]
+    int32_t *tile_done, *tile_ctr, *tile_par;
+    double *partial;       // [ntiles][bpt][NDOT*T]
     int32_t *remaining;    // tiles not yet converged
     int32_t *status;       // first error code
     double *terms;         // per column Re sum alpha_l pi_l
     const double *class_size; // |colour class| per column (0 for padding)
-    double *result;        // [0] = sum of terms
+    double *result;        // [0] = sum of terms, [1] = sum of seed projections
 };
+
+// dot products per column reduced each pass: r.r, p.w, r.w, w.w, v.r, v.w
+constexpr int NDOT = 6;
 
 // Engine entry points (engine.cu); all asynchronous on `stream`.
 int engine_init(const Solve &s, int col_begin, int col_end, void *stream);
-int engine_iteration(const Solve &s, int parity, void *stream);      // phase A + phase B
+int engine_iteration(const Solve &s, int parity, void *stream);      // one fused CG pass
 int engine_cta_solve(const Solve &s, int max_iter, void *stream);    // whole solve, one CTA per tile
+int engine_flush_x(const Solve &s, void *stream);                    // last seed-solution update
 int engine_finish(const Solve &s, int col_begin, int col_end, void *stream);
 int engine_apply(const Operator &op, int precision, int T, int ntiles, const void *x, void *y,
                  void *stream);
 int engine_grad_params(const Solve &s, int nparam, const int *ids, double *out_dev, void *stream);
-int engine_blocks_per_tile(const Solve &s);
+int engine_plan(Solve &s);   // sets bpt (and strips/seg); returns bpt
 const char *engine_error_string(int cuda_err);
 
 }  // namespace ld
