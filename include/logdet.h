@@ -205,6 +205,36 @@ ld_status ld_batch_create(int count, const ld_matrix *Qs, const int *distances, 
 /* logdets[count]; grads[count] (d/d kappa2, may be NULL); infos may be NULL. */
 ld_status ld_batch_logdet(ld_ctx *ctx, double *logdets, double *grads, ld_info *info);
 
+/* ---------------------------------------------------------------------------
+ * Evaluation without device allocation (no counterpart in the paper).
+ *
+ * For callers that may not call cudaMalloc/cudaFree when they need a log det,
+ * e.g. code running under a framework allocator or memory arena that owns all
+ * device memory, or a latency-critical callback where an allocation would
+ * synchronise the device.  Every work buffer lives in one static device array
+ * of LD_STATIC_SCRATCH_BYTES that each GPU loading the library keeps until the
+ * process exits; the call allocates nothing (no cudaMalloc, cudaFree or
+ * allocating library routine) and copies its inputs into that array.
+ *
+ *   Q          grid kinds 2D5, 2D13_SQ, 3D7 with scalar kappa2, no field, no mask.
+ *   colour     host, n ints in [0, n_colours): the probing colouring (e.g. from
+ *              ld_colour_grid); n_colours <= LD_STATIC_MAX_COLOURS.
+ *   n_shifts   quadrature nodes (1..256); tol, max_iter as in ld_create/ld_options.
+ *   cuda_stream stream to run on (NULL = default stream); the call synchronises it.
+ *   logdet     host output, written on LD_OK.
+ * Runs the same probed rational-log multi-shift CG as ld_logdet in FP64 with one
+ * CTA per probing vector (small problems).  Needs 48*n*n_colours bytes plus small
+ * tables inside the array; larger problems return LD_EINVAL ("needs more than
+ * LD_STATIC_SCRATCH_BYTES").  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress): make that first call outside any stream
+ * capture.  Every call shares the one array and leaves its contents behind (the
+ * call clears what must start at zero): calls that overlap on the GPU, from two
+ * threads or two streams, race and corrupt each other. */
+#define LD_STATIC_SCRATCH_BYTES (8u << 20)
+#define LD_STATIC_MAX_COLOURS 1024
+ld_status ld_logdet_static(const ld_matrix *Q, const int32_t *colour, int n_colours, int n_shifts,
+                           double tol, int max_iter, void *cuda_stream, double *logdet);
+
 /* Message for the last failure on this thread; never NULL. */
 const char *ld_last_error(void);
 

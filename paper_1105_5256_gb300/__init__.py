@@ -99,6 +99,7 @@ def library(build_if_missing: bool = False):
         "ld_grid_bounds": ([P(Matrix), P(dbl), P(dbl)], st),
         "ld_batch_create": ([C.c_int, vp, vp, C.c_int, dbl, P(Options), P(vp)], st),
         "ld_batch_logdet": ([vp, vp, vp, vp], st),
+        "ld_logdet_static": ([P(Matrix), vp, C.c_int, C.c_int, dbl, C.c_int, vp, P(dbl)], st),
         "ld_last_error": ([], C.c_char_p),
         "ld_destroy": ([vp], None),
     }
@@ -334,6 +335,20 @@ def ld_batch_logdet(ctx: Context, with_grad: bool = False):
     info = Info()
     _check(library().ld_batch_logdet(ctx.handle, _ptr(out), _ptr(g), C.byref(info)))
     return out, g, info.as_dict()
+
+
+def ld_logdet_static(matrix, colour, n_colours: int, n_shifts: int, tol: float,
+                     max_iter: int = 100000, cuda_stream=None) -> float:
+    """log det with no device allocation (scratch in the library's static device
+    array; see the header for limits and for the first-call and overlap rules)."""
+    m, _ = matrix
+    col = np.ascontiguousarray(colour, dtype=np.int32)
+    v = C.c_double()
+    _check(library().ld_logdet_static(C.byref(m), _ptr(col), int(n_colours), int(n_shifts),
+                                      float(tol), int(max_iter),
+                                      C.c_void_p(int(cuda_stream)) if cuda_stream else None,
+                                      C.byref(v)))
+    return v.value
 
 
 def ld_destroy(ctx: Context):

@@ -17,7 +17,7 @@ OUT = os.path.join(PKG, "liblogdet.so")
 BUILD = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["engine.cu"]
+CU_SOURCES = ["engine.cu", "static_scratch.cu"]
 CXX_SOURCES = ["api.cpp", "colouring.cpp", "hht.cpp"]
 
 

@@ -70,6 +70,8 @@ struct DevBuf {
 
 }  // namespace
 
+void ld::set_last_error(const char *msg) { g_err = msg; }
+
 struct ld_ctx {
     // problem
     int kind = 0, periodic = 0;

@@ -12,6 +12,7 @@ namespace ld {
 enum { KIND_CSR = 0, KIND_2D5 = 1, KIND_2D13_SQ = 2, KIND_3D7 = 3 };
 
 // ---------------------------------------------------------------- host helpers
+void set_last_error(const char *msg);   // message returned by ld_last_error() on this thread
 int colour_csr(int64_t n, const int64_t *rowptr, const int32_t *colidx, int d, int32_t *colour);
 int colour_grid(int kind, const int32_t dims[3], int periodic, int d, int32_t *colour);
 double ellip_k(double m);
