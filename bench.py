@@ -43,6 +43,8 @@ SEED = 2
 METRIC = "log-det(+grad) evals/sec (Matern 1024^2, probing d=2, N=20)"
 UNIT = "evals/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP64_FLOPS_PER_VC = 33          # 13-point pass: combine, two difference-form levels, dots
+FP64_PEAK_GFLOPS = 1250.0       # measured non-tensor FP64 rate of a GB300
 
 
 def peak_hbm():
@@ -105,15 +107,32 @@ def dist_env():
     return ws, rank, local
 
 
-def iteration_bytes(n, ncols, ntiles, prec):
-    """Algorithmic HBM bytes of one fused CG pass, per tile-iteration.
+def algorithmic_bytes(n, T, prec, tile_iters, passes):
+    """Algorithmic HBM bytes of the CG passes of a solve.
 
-    The pass reads r, w, p of one set and writes r, w, p of the other (6 vector passes of
-    n*T words) and reads each vertex's colour (4 bytes).  Halo re-reads are not counted.
+    A pass reads r, w, p of one set and writes r, w, p of the other: 6 vector passes of
+    n*T words per active tile (tile_iters counts tile-passes), plus each vertex's colour
+    once per pass (4 bytes).  Halo re-reads are not counted.
     """
     w = 8 if prec == "fp64" else 4
-    T = ncols // ntiles
-    return 6 * n * T * w + 4 * n
+    return 6 * n * T * w * tile_iters + 4 * n * passes
+
+
+def recorded_traffic(tile_width):
+    """DRAM bytes per full launch of the pass kernel from the committed ncu summary, or
+    None when the engine source changed since that capture (or no summary matches)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_stream2d_matern1024_T%d.md" % tile_width)
+    src = os.path.join(ROOT, "paper_1105_5256_gb300", "csrc", "engine.cu")
+    try:
+        rec = dict(line.split(": ", 1) for line in open(path).read().splitlines()
+                   if line.startswith(("engine_sha256: ", "traffic_bytes_per_launch: ")))
+        cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if rec.get("engine_sha256", "").strip() != cur:
+            return None
+        return float(rec["traffic_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def run_ours(args):
@@ -183,12 +202,25 @@ def run_ours(args):
     value = evals / (dev_ms / 1e3)
     e2e = evals / wall
     info0 = all_infos[0]
-    ncols = ((info0["n_colours"] + info0["tile_width"] - 1) // info0["tile_width"]) * info0["tile_width"]
-    ntiles = ncols // info0["tile_width"]
-    bytes_tile_iter = iteration_bytes(n, ncols, ntiles, args.precision)
-    achieved = bytes_tile_iter * tile_iters / (iter_ms / 1e3) / 1e9
+    T = info0["tile_width"]
+    ncols = ((info0["n_colours"] + T - 1) // T) * T
+    ntiles = ncols // T
+    passes = sum(i["iters"] for i in all_infos)
+    alg = algorithmic_bytes(n, T, args.precision, tile_iters, passes)
+    achieved = alg / (iter_ms / 1e3) / 1e9
     peak, src = peak_hbm()
-    traffic = None
+    traffic = recorded_traffic(T) if args.precision == "mixed" else None
+    if args.precision == "fp64":
+        # FP64 issue-bound: 33 flops per vertex-column per pass against the measured
+        # 1.25 TFLOP/s non-tensor FP64 rate
+        flops = FP64_FLOPS_PER_VC * n * T * tile_iters
+        roof = {"bound": "alu", "kernel": "fused CG pass (k_stream2d, FP64)",
+                "achieved": flops / (iter_ms / 1e3) / 1e9, "peak": FP64_PEAK_GFLOPS,
+                "unit": "GFLOP/s", "traffic": None,
+                "peak_source": "measured FP64 FMA-chain rate (equals the nominal 1.25 TFLOP/s)"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    else:
+        roof = None
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
@@ -206,18 +238,38 @@ def run_ours(args):
                 "h2d_bytes_per_step": args.batch * (3 * 8 + 2 * NSHIFT * 16),
                 "d2h_bytes_per_step": args.batch * (2 * 8 + 2 * 4 + 4 * ncols)},
         "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "kernel": "fused CG pass (k_stream2d)",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "peak_source": src},
+        "roofline": roof or {"bound": "hbm", "kernel": "fused CG pass (k_stream2d)",
+                             "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": traffic,
+                             "algorithmic_bytes_per_launch": algorithmic_bytes(n, T, args.precision, ntiles, 1),
+                             "peak_source": src},
         "iters_mean": float(np.mean([i["iters"] for i in all_infos])),
         "logdet_first": vals[0],
     }
+    if rank == 0 and ws == 1 and args.precision == "mixed" and args.fp64_sample > 0:
+        out["fp64_form"] = fp64_form(L, draws[:args.fp64_sample], vals[:args.fp64_sample])
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def fp64_form(L, draws, mixed_vals):
+    """The plain FP64 form on the first draws of the batch: evaluations per second and
+    the largest relative difference of the mixed-precision values from it."""
+    ctx = L.ld_create(L.grid_matrix(L.LD_STENCIL_2D13_SQ, DIMS, float(draws[0])), DIST, NSHIFT,
+                      TOL, L.options(precision=L.LD_FP64))
+    ms = 0.0
+    rel = 0.0
+    for k2, vm in zip(draws, mixed_vals):
+        L.ld_set_params(ctx, float(k2))
+        v, info = L.ld_logdet(ctx)
+        ms += info["ms"]
+        rel = max(rel, abs(vm - v) / abs(v))
+    return {"value": len(draws) / (ms / 1e3), "unit": UNIT, "evaluations": len(draws),
+            "kappa2": [float(k) for k in draws], "mixed_vs_fp64_rel_diff_max": rel}
 
 
 def cpu_baseline(budget_s: float):
@@ -282,6 +334,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=BATCH, help="kappa^2 values per step")
     ap.add_argument("--tile-width", type=int, default=0, help="probing vectors per tile (0 = auto)")
+    ap.add_argument("--fp64-sample", type=int, default=2,
+                    help="draws also evaluated in the plain FP64 form (mixed precision runs)")
     ap.add_argument("--kappa2", type=float, default=0.0,
                     help="fixed kappa^2 for every evaluation (profiling runs); 0 = seeded draws")
     args = ap.parse_args()

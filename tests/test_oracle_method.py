@@ -199,3 +199,18 @@ def test_probing_error_shrinks_with_distance():
         col = probing.colour_greedy(Q, d)
         errs.append(abs(cf.probed_value(om.KIND_2D5, dims, 0.05, True, col, np.log) - exact))
     assert all(e2 < e1 for e1, e2 in zip(errs, errs[1:]))
+
+
+def test_banded_shifted_solves_equal_dense_rational_target():
+    """Complex-symmetric banded LDL^T quadratic forms == dense eigendecomposition of f_N."""
+    n = 150
+    import synth
+    rows, cols, w = synth.random_sparse_spd_pattern(31, n)
+    rp, ci, vv = synth.csr_from_edges(n, rows, cols, w, 0.4)
+    Q = sp.csr_matrix((vv, ci, rp), shape=(n, n))
+    ev = np.linalg.eigvalsh(Q.toarray())
+    sigma, alpha = hht.log_nodes(0.9 * ev.min(), 1.1 * ev.max(), 16)
+    col = probing.colour_greedy(Q, 2)
+    band = mt.probed_rational_band(Q, col, sigma, alpha)
+    dense = mt.probed_dense(Q, col, lambda lam: hht.f_N(lam, sigma, alpha))
+    assert abs(band - dense) <= 1e-11 * abs(dense)
