@@ -26,6 +26,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -660,6 +661,91 @@ __device__ __forceinline__ Pack<V, TS> zero_pack() {
     return z;
 }
 
+// ---- elementwise pack arithmetic; FP32 pairs issue as one packed f32x2 instruction
+template <typename V, int TS>
+struct PackMath {
+    using P = Pack<V, TS>;
+    static constexpr bool kPaired = std::is_same<V, float>::value && TS % 2 == 0;
+    __device__ static __forceinline__ unsigned long long &u(P &a, int j) {
+        return reinterpret_cast<unsigned long long *>(a.v)[j];
+    }
+    __device__ static __forceinline__ unsigned long long cu(const P &a, int j) {
+        return reinterpret_cast<const unsigned long long *>(a.v)[j];
+    }
+    __device__ static __forceinline__ P fma(const P &a, const P &b, const P &c) {
+        P o;
+        if constexpr (kPaired) {
+#pragma unroll
+            for (int j = 0; j < TS / 2; ++j)
+                asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(u(o, j)) : "l"(cu(a, j)), "l"(cu(b, j)), "l"(cu(c, j)));
+        } else {
+#pragma unroll
+            for (int t = 0; t < TS; ++t) o.v[t] = ::fma(a.v[t], b.v[t], c.v[t]);
+        }
+        return o;
+    }
+    __device__ static __forceinline__ P add(const P &a, const P &b) {
+        P o;
+        if constexpr (kPaired) {
+#pragma unroll
+            for (int j = 0; j < TS / 2; ++j)
+                asm("add.rn.f32x2 %0, %1, %2;" : "=l"(u(o, j)) : "l"(cu(a, j)), "l"(cu(b, j)));
+        } else {
+#pragma unroll
+            for (int t = 0; t < TS; ++t) o.v[t] = a.v[t] + b.v[t];
+        }
+        return o;
+    }
+    __device__ static __forceinline__ P sub(const P &a, const P &b) {
+        P o;
+        if constexpr (kPaired) {
+#pragma unroll
+            for (int j = 0; j < TS / 2; ++j)
+                asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(u(o, j)) : "l"(cu(a, j)), "l"(cu(b, j)));
+        } else {
+#pragma unroll
+            for (int t = 0; t < TS; ++t) o.v[t] = a.v[t] - b.v[t];
+        }
+        return o;
+    }
+    __device__ static __forceinline__ P mul(const P &a, const P &b) {
+        P o;
+        if constexpr (kPaired) {
+#pragma unroll
+            for (int j = 0; j < TS / 2; ++j)
+                asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(u(o, j)) : "l"(cu(a, j)), "l"(cu(b, j)));
+        } else {
+#pragma unroll
+            for (int t = 0; t < TS; ++t) o.v[t] = a.v[t] * b.v[t];
+        }
+        return o;
+    }
+    __device__ static __forceinline__ P splat(V x) {
+        P o;
+#pragma unroll
+        for (int t = 0; t < TS; ++t) o.v[t] = x;
+        return o;
+    }
+    __device__ static __forceinline__ P neg(const P &a) {
+        P o;
+#pragma unroll
+        for (int t = 0; t < TS; ++t) o.v[t] = -a.v[t];
+        return o;
+    }
+};
+
+// c p + ((p - l) + (p - r)) + ((p - d) + (p - u)): one level of the difference-form stencil,
+// c a pack (per-vertex diagonal or kappa2 splat)
+template <typename V, int TS>
+__device__ __forceinline__ Pack<V, TS> diff5p(const Pack<V, TS> &c, const Pack<V, TS> &pc,
+                                              const Pack<V, TS> &pl, const Pack<V, TS> &pr,
+                                              const Pack<V, TS> &pd, const Pack<V, TS> &pu) {
+    using M = PackMath<V, TS>;
+    const Pack<V, TS> h = M::add(M::sub(pc, pl), M::sub(pc, pr));
+    const Pack<V, TS> v = M::add(M::sub(pc, pd), M::sub(pc, pu));
+    return M::fma(c, pc, M::add(h, v));
+}
+
 // (c p + sum of the four differences), the difference-form stencil of one level
 template <typename V, int TS>
 __device__ __forceinline__ Pack<V, TS> diff5(V c, const Pack<V, TS> &pc, const Pack<V, TS> &pl,
@@ -719,14 +805,17 @@ __global__ void __launch_bounds__(SW * G, stream_min_blocks_t<V, T>()) k_stream2
     const V *const r = static_cast<const V *>(cur ? s.rbuf[1] : s.rbuf[0]) + off;
     const V *const w = static_cast<const V *>(cur ? s.wbuf[1] : s.wbuf[0]) + off;
     const V *const p = static_cast<const V *>(cur ? s.pbuf[1] : s.pbuf[0]) + off;
-    V a[TS], b[TS];
-    V d_rr[TS], d_pw[TS], d_rw[TS], d_ww[TS], d_vr[TS], d_vw[TS];
+    using M = PackMath<V, TS>;
+    P na, b;                  // -alpha, beta per column
+    P d_rr, d_pw, d_rw, d_ww; // dot accumulators
+    V d_vr[TS], d_vw[TS];
 #pragma unroll
     for (int t = 0; t < TS; ++t) {
-        a[t] = (V)s.alpha[cb + t];
-        b[t] = (V)s.beta[cb + t];
-        d_rr[t] = d_pw[t] = d_rw[t] = d_ww[t] = d_vr[t] = d_vw[t] = (V)0;
+        na.v[t] = -(V)s.alpha[cb + t];
+        b.v[t] = (V)s.beta[cb + t];
+        d_vr[t] = d_vw[t] = (V)0;
     }
+    d_rr = d_pw = d_rw = d_ww = zero_pack<V, TS>();
     P pw0 = zero_pack<V, TS>(), pw1 = pw0, pw2 = pw0;   // p at rows y-2, y-1, y
     P uw0 = pw0, uw1 = pw0, uw2 = pw0;                   // u at rows y-3, y-2, y-1
 
@@ -752,10 +841,7 @@ __global__ void __launch_bounds__(SW * G, stream_min_blocks_t<V, T>()) k_stream2
     // outputs at (gx, y) of lattice row y held in ring slot `slot`
     auto emit = [&](int y, int slot, const P &pk, const P &wk) {
         const P *q = ring + slot * 3 * NT;
-        const P r0 = q[0], w0 = q[NT];
-        P rk;
-#pragma unroll
-        for (int t = 0; t < TS; ++t) rk.v[t] = fma(-a[t], w0.v[t], r0.v[t]);
+        const P rk = M::fma(na, q[NT], q[0]);
         const int64_t gi = (int64_t)y * nx + gx;
         const int64_t e = gi * T;
         V *rn = static_cast<V *>(cur ? s.rbuf[0] : s.rbuf[1]) + off;
@@ -766,19 +852,16 @@ __global__ void __launch_bounds__(SW * G, stream_min_blocks_t<V, T>()) k_stream2
         *reinterpret_cast<P *>(wn + e) = wk;
         if constexpr (KEEPX) {
             V *x = static_cast<V *>(s.x) + off;
-            const P p0 = q[2 * NT];
-            P xo = *reinterpret_cast<const P *>(x + e);
-#pragma unroll
-            for (int t = 0; t < TS; ++t) xo.v[t] = fma(a[t], p0.v[t], xo.v[t]);
-            *reinterpret_cast<P *>(x + e) = xo;
+            const P xo = *reinterpret_cast<const P *>(x + e);
+            *reinterpret_cast<P *>(x + e) = M::fma(M::neg(na), q[2 * NT], xo);
         }
         const int lc = ringc[slot * NT] - cb;
+        d_rr = M::fma(rk, rk, d_rr);
+        d_pw = M::fma(pk, wk, d_pw);
+        d_rw = M::fma(rk, wk, d_rw);
+        d_ww = M::fma(wk, wk, d_ww);
 #pragma unroll
         for (int t = 0; t < TS; ++t) {
-            d_rr[t] = fma(rk.v[t], rk.v[t], d_rr[t]);
-            d_pw[t] = fma(pk.v[t], wk.v[t], d_pw[t]);
-            d_rw[t] = fma(rk.v[t], wk.v[t], d_rw[t]);
-            d_ww[t] = fma(wk.v[t], wk.v[t], d_ww[t]);
             if (lc == t) {
                 d_vr[t] += rk.v[t];
                 d_vw[t] += wk.v[t];
@@ -798,19 +881,16 @@ __global__ void __launch_bounds__(SW * G, stream_min_blocks_t<V, T>()) k_stream2
         cp_async_wait<PD - 1 - H>();
         {
             const P *q = ring + slot * 3 * NT;
-            const P r0 = q[0], w0 = q[NT], p0 = q[2 * NT];
-            P pk;
-#pragma unroll
-            for (int t = 0; t < TS; ++t) pk.v[t] = fma(b[t], p0.v[t], fma(-a[t], w0.v[t], r0.v[t]));
+            const P pk = M::fma(b, q[2 * NT], M::fma(na, q[NT], q[0]));
             ps[(y & 1) * NT + threadIdx.x] = pk;
             pw0 = pw1;
             pw1 = pw2;
             pw2 = pk;
         }
         const int slot_h = slot - H < 0 ? slot - H + PD : slot - H;   // slot of row y - H
-        const V sc = (V)s.op.scale;
+        const P sc = M::splat((V)s.op.scale);
         if constexpr (KIND == KIND_2D13_SQ) {
-            const V k2 = (V)s.op.kappa2;
+            const P k2 = M::splat((V)s.op.kappa2);
             // u = Q1 p at (x, y-1): p row y-1 was shared last step
             if (y >= ys) {
                 P u = zero_pack<V, TS>();
@@ -818,7 +898,7 @@ __global__ void __launch_bounds__(SW * G, stream_min_blocks_t<V, T>()) k_stream2
                 wrap_coord(y - 1, ny, per, uin);
                 if (uin && inx && xl >= 1 && xl < SW - 1) {
                     const P *row = ps + ((y - 1) & 1) * NT;
-                    u = diff5<V, TS>(k2, pw1, row[threadIdx.x - G], row[threadIdx.x + G], pw0, pw2);
+                    u = diff5p<V, TS>(k2, pw1, row[threadIdx.x - G], row[threadIdx.x + G], pw0, pw2);
                 }
                 us[((y - 1) & 1) * NT + threadIdx.x] = u;
                 uw0 = uw1;
@@ -828,9 +908,7 @@ __global__ void __launch_bounds__(SW * G, stream_min_blocks_t<V, T>()) k_stream2
             // w = Q1 u at (x, y-2): u row y-2 was shared last step
             if (y - 2 >= ys && y - 2 < ye && outx) {
                 const P *row = us + ((y - 2) & 1) * NT;
-                P wk = diff5<V, TS>(k2, uw1, row[threadIdx.x - G], row[threadIdx.x + G], uw0, uw2);
-#pragma unroll
-                for (int t = 0; t < TS; ++t) wk.v[t] *= sc;
+                const P wk = M::mul(sc, diff5p<V, TS>(k2, uw1, row[threadIdx.x - G], row[threadIdx.x + G], uw0, uw2));
                 emit(y - 2, slot_h, pw0, wk);
             }
         } else {
@@ -840,9 +918,7 @@ __global__ void __launch_bounds__(SW * G, stream_min_blocks_t<V, T>()) k_stream2
                 V dg = field_at<V>(s.op, gi);
                 if (s.op.mask) dg += (V)s.op.tau * (V)s.op.mask[gi];
                 const P *row = ps + ((y - 1) & 1) * NT;
-                P wk = diff5<V, TS>(dg, pw1, row[threadIdx.x - G], row[threadIdx.x + G], pw0, pw2);
-#pragma unroll
-                for (int t = 0; t < TS; ++t) wk.v[t] *= sc;
+                const P wk = M::mul(sc, diff5p<V, TS>(M::splat(dg), pw1, row[threadIdx.x - G], row[threadIdx.x + G], pw0, pw2));
                 emit(y - 1, slot_h, pw1, wk);
             }
         }
@@ -860,10 +936,10 @@ __global__ void __launch_bounds__(SW * G, stream_min_blocks_t<V, T>()) k_stream2
         V *mine = part + threadIdx.x * NDOT * TS;
 #pragma unroll
         for (int t = 0; t < TS; ++t) {
-            mine[0 * TS + t] = d_rr[t];
-            mine[1 * TS + t] = d_pw[t];
-            mine[2 * TS + t] = d_rw[t];
-            mine[3 * TS + t] = d_ww[t];
+            mine[0 * TS + t] = d_rr.v[t];
+            mine[1 * TS + t] = d_pw.v[t];
+            mine[2 * TS + t] = d_rw.v[t];
+            mine[3 * TS + t] = d_ww.v[t];
             mine[4 * TS + t] = d_vr[t];
             mine[5 * TS + t] = d_vw[t];
         }
