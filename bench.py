@@ -135,6 +135,42 @@ def recorded_traffic(tile_width):
         return None
 
 
+def run_batch(args):
+    """Secondary workload: 256 independent 2D GMRFs of uneven size (sides 32..512,
+    5-point d=4 or 13-point d=2, kappa^2 log-uniform) in one persistent launch per step;
+    mixed precision, with the same batch in the plain FP64 form beside it."""
+    import torch
+    import paper_1105_5256_gb300 as L
+    torch.cuda.set_device(0)
+    L.library(build_if_missing=True)
+    insts = synth.batch_instances(3, count=256)
+    mats = [L.grid_matrix(i.kind, i.dims, i.kappa2) for i in insts]
+    dists = [i.distance for i in insts]
+    out = {}
+    for name, prec in (("mixed", L.LD_MIXED), ("fp64", L.LD_FP64)):
+        b = L.ld_batch_create(mats, dists, NSHIFT, TOL, L.options(precision=prec))
+        for _ in range(args.warmup):
+            L.ld_batch_logdet(b)
+        ms = 0.0
+        for _ in range(args.steps):
+            vals, _, info = L.ld_batch_logdet(b)
+            ms += info["ms"]
+        out[name] = {"value": 256 * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+                     "vals": vals}
+        del b
+    rel = float(np.max(np.abs(out["mixed"]["vals"] - out["fp64"]["vals"]) / np.abs(out["fp64"]["vals"])))
+    line = {"metric": "log-det evals/sec (batch of 256 uneven 2D GMRFs, one persistent launch)",
+            "value": out["mixed"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": out["mixed"]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 vectors / f64 scalars", "data": "synthetic (seeded batch)",
+            "config": {"workload": "256 grids, sides U{32..512}, 5-pt d=4 / 13-pt d=2, N=20, tol 1e-6",
+                       "points": int(sum(i.n for i in insts))},
+            "fp64_form": {"value": out["fp64"]["value"], "ms_per_step": out["fp64"]["ms_per_step"],
+                          "mixed_vs_fp64_rel_diff_max": rel}}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import torch
     import paper_1105_5256_gb300 as L
@@ -334,6 +370,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=BATCH, help="kappa^2 values per step")
     ap.add_argument("--tile-width", type=int, default=0, help="probing vectors per tile (0 = auto)")
+    ap.add_argument("--workload", default="matern1024", choices=["matern1024", "batch256"])
     ap.add_argument("--fp64-sample", type=int, default=2,
                     help="draws also evaluated in the plain FP64 form (mixed precision runs)")
     ap.add_argument("--kappa2", type=float, default=0.0,
@@ -341,6 +378,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch256":
+        run_batch(args)
     else:
         run_ours(args)
 

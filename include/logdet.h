@@ -197,12 +197,20 @@ ld_status ld_hht_nodes(double lmin, double lmax, int N, double *sigma, double *a
 /* Spectral interval the library uses for a grid kind (Weyl bounds). */
 ld_status ld_grid_bounds(const ld_matrix *Q, double *lmin, double *lmax);
 
-/* Batched evaluation of many independent grid GMRFs in one persistent launch
- * (each (instance, tile) a work item).  Qs[count], distances[count] as in ld_create. */
+/* Batched evaluation of many independent grid GMRFs of uneven size in one persistent
+ * launch (each (instance, tile) a work item).  Qs[count] (grid kinds), distances[count]
+ * as in ld_create; every instance gets its own colouring, spectral bounds and nodes.
+ * opt: precision, max_iter, tile_width (0 = 2 for mixed, 1 for FP64), cuda_stream.
+ * Errors: as ld_create, reported with the failing instance's index. */
 ld_status ld_batch_create(int count, const ld_matrix *Qs, const int *distances, int n_shifts,
                           double tol, const ld_options *opt, ld_ctx **out);
 
-/* logdets[count]; grads[count] (d/d kappa2, may be NULL); infos may be NULL. */
+/* Evaluate every instance: logdets[count]; grads[count] = d log det / d kappa2 for
+ * scalar-kappa2 5/7-point instances (tr Q^{-1} probed, from the projected seed sums),
+ * NaN for the others; grads and info may be NULL.  One CUDA-graph launch: a queue
+ * reset, a per-instance prep kernel, the persistent solve (CTAs pull (instance, tile)
+ * items, longest first, and run each tile's whole CG-M in one CTA) and a per-instance
+ * sum.  Errors: the first failing instance's status (no outputs written). */
 ld_status ld_batch_logdet(ld_ctx *ctx, double *logdets, double *grads, ld_info *info);
 
 /* ---------------------------------------------------------------------------

@@ -112,8 +112,16 @@ struct ld_ctx {
     bool have_x0 = false;
     int last_cb = 0, last_ce = 0;
     bool solved = false;
+    // batch mode: independent problems solved by one persistent launch
+    bool is_batch = false;
+    std::vector<ld_ctx *> subs;
+    DevBuf d_solves, d_items, d_queue, d_bout, d_bint;
+    int nitems = 0, bgrid = 0;
+    cudaGraphExec_t bgraph = nullptr;
 
     ~ld_ctx() {
+        if (bgraph) cudaGraphExecDestroy(bgraph);
+        for (ld_ctx *c : subs) delete c;
         if (graph) cudaGraphExecDestroy(graph);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
@@ -634,6 +642,7 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
 
 ld_status ld_set_params(ld_ctx *c, double kappa2, double tau, double scale) {
     if (!c) return fail(LD_EINVAL, "ctx is NULL");
+    if (c->is_batch) return fail(LD_EINVAL, "batched context: use ld_batch_logdet");
     if (c->kind == LD_CSR) return fail(LD_EUNSUPPORTED, "CSR contexts have fixed values");
     if (!std::isfinite(kappa2) || kappa2 < 0.0) return fail(LD_EINVAL, "kappa2 must be finite and >= 0");
     if (!std::isfinite(tau) || tau < 0.0) return fail(LD_EINVAL, "tau must be finite and >= 0");
@@ -659,6 +668,7 @@ ld_status ld_set_params(ld_ctx *c, double kappa2, double tau, double scale) {
 
 ld_status ld_logdet(ld_ctx *c, double *logdet, ld_info *info) {
     if (!c || !logdet) return fail(LD_EINVAL, "ctx and logdet must be non-NULL");
+    if (c->is_batch) return fail(LD_EINVAL, "batched context: use ld_batch_logdet");
     double out[2];
     ld_status st = run_solve(c, 0, c->ncolours, c->opt.keep_x0 != 0, out, info);
     if (st == LD_OK) *logdet = out[0];
@@ -667,6 +677,7 @@ ld_status ld_logdet(ld_ctx *c, double *logdet, ld_info *info) {
 
 ld_status ld_grad(ld_ctx *c, int n_params, const int *ids, double *grad) {
     if (!c || !grad) return fail(LD_EINVAL, "ctx and grad must be non-NULL");
+    if (c->is_batch) return fail(LD_EINVAL, "batched context: use ld_batch_logdet");
     if (ld_status v = check_params(c, n_params, ids)) return v;
     if (!c->have_x0) return fail(LD_EINVAL, "no seed solutions saved: run ld_logdet on a keep_x0 context first");
     double *d_out = c->s.result + 2;
@@ -684,6 +695,7 @@ ld_status ld_grad(ld_ctx *c, int n_params, const int *ids, double *grad) {
 ld_status ld_logdet_grad(ld_ctx *c, int n_params, const int *ids, double *logdet, double *grad,
                          ld_info *info) {
     if (!c || !logdet || !grad) return fail(LD_EINVAL, "ctx, logdet and grad must be non-NULL");
+    if (c->is_batch) return fail(LD_EINVAL, "batched context: use ld_batch_logdet");
     if (ld_status v = check_params(c, n_params, ids)) return v;
     // d/d kappa2 of a scalar-kappa2 5/7-point grid is tr(Q^{-1}) * scale: the projected
     // seed sum v^T Q^{-1} v needs no stored seed vectors.
@@ -705,6 +717,7 @@ ld_status ld_logdet_grad(ld_ctx *c, int n_params, const int *ids, double *logdet
 
 ld_status ld_logdet_partial(ld_ctx *c, int cb, int ce, double *partial, ld_info *info) {
     if (!c || !partial) return fail(LD_EINVAL, "ctx and partial must be non-NULL");
+    if (c->is_batch) return fail(LD_EINVAL, "batched context: use ld_batch_logdet");
     if (cb < 0 || ce < cb || ce > c->ncolours) return fail(LD_EINVAL, "colour range [%d, %d) outside [0, %d)", cb, ce, c->ncolours);
     double out[2];
     ld_status st = run_solve(c, cb, ce, c->opt.keep_x0 != 0, out, info);
@@ -714,6 +727,7 @@ ld_status ld_logdet_partial(ld_ctx *c, int cb, int ce, double *partial, ld_info 
 
 ld_status ld_column_terms(const ld_ctx *c, double *terms, double *seed) {
     if (!c || !terms) return fail(LD_EINVAL, "ctx and terms must be non-NULL");
+    if (c->is_batch) return fail(LD_EINVAL, "batched context: use ld_batch_logdet");
     if (!c->solved) return fail(LD_EINVAL, "no completed solve on this context");
     CUDA_TRY(cudaMemcpy(terms, c->s.terms, c->ncolours * sizeof(double), cudaMemcpyDeviceToHost));
     if (seed) CUDA_TRY(cudaMemcpy(seed, c->s.pi0, c->ncolours * sizeof(double), cudaMemcpyDeviceToHost));
@@ -722,6 +736,7 @@ ld_status ld_column_terms(const ld_ctx *c, double *terms, double *seed) {
 
 ld_status ld_get_colouring(const ld_ctx *c, int32_t *colour, int32_t *n_colours) {
     if (!c) return fail(LD_EINVAL, "ctx is NULL");
+    if (c->is_batch) return fail(LD_EINVAL, "batched context: use ld_batch_logdet");
     if (colour) std::memcpy(colour, c->colour.data(), c->n * sizeof(int32_t));
     if (n_colours) *n_colours = c->ncolours;
     return LD_OK;
@@ -729,6 +744,7 @@ ld_status ld_get_colouring(const ld_ctx *c, int32_t *colour, int32_t *n_colours)
 
 ld_status ld_get_nodes(const ld_ctx *c, double *sigma, double *alpha, int32_t *n_shifts) {
     if (!c) return fail(LD_EINVAL, "ctx is NULL");
+    if (c->is_batch) return fail(LD_EINVAL, "batched context: use ld_batch_logdet");
     for (int l = 0; l < c->nshift; ++l) {
         if (sigma) { sigma[2 * l] = c->sigma[l].real(); sigma[2 * l + 1] = c->sigma[l].imag(); }
         if (alpha) { alpha[2 * l] = c->alpha[l].real(); alpha[2 * l + 1] = c->alpha[l].imag(); }
@@ -739,6 +755,7 @@ ld_status ld_get_nodes(const ld_ctx *c, double *sigma, double *alpha, int32_t *n
 
 ld_status ld_apply(ld_ctx *c, int ncols, const double *x, double *y) {
     if (!c || !x || !y || ncols < 1) return fail(LD_EINVAL, "bad arguments");
+    if (c->is_batch) return fail(LD_EINVAL, "batched context: use ld_batch_logdet");
     const int T = c->T;
     const int nt = (ncols + T - 1) / T;
     const int64_t n = c->n;
@@ -831,14 +848,153 @@ ld_status ld_grid_bounds(const ld_matrix *Q, double *lmin, double *lmax) {
     return LD_OK;
 }
 
-ld_status ld_batch_create(int, const ld_matrix *, const int *, int, double, const ld_options *,
-                          ld_ctx **out) {
-    if (out) *out = nullptr;
-    return fail(LD_EUNSUPPORTED, "batched contexts are not available in this build");
+ld_status ld_batch_create(int count, const ld_matrix *Qs, const int *distances, int n_shifts,
+                          double tol, const ld_options *opt_in, ld_ctx **out) {
+    if (!out) return fail(LD_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !Qs || !distances) return fail(LD_EINVAL, "count >= 1 with Qs and distances");
+    ld_options opt;
+    ld_default_options(&opt);
+    if (opt_in) opt = *opt_in;
+    if (opt.precision != LD_FP64 && opt.precision != LD_MIXED) return fail(LD_EINVAL, "bad precision");
+    ld_ctx *c = new (std::nothrow) ld_ctx();
+    if (!c) return fail(LD_ENOMEM, "host allocation");
+    std::unique_ptr<ld_ctx> guard(c);
+    c->is_batch = true;
+    c->opt = opt;
+    c->nshift = n_shifts;
+    c->tol = tol;
+    if (opt.cuda_stream) {
+        c->stream = static_cast<cudaStream_t>(opt.cuda_stream);
+    } else {
+        CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    CUDA_TRY(cudaEventCreate(&c->ev0));
+    CUDA_TRY(cudaEventCreate(&c->ev1));
+    // every instance: a one-CTA-per-tile context with a common tile width
+    ld_options sub = opt;
+    sub.engine = 2;
+    sub.keep_x0 = 0;
+    sub.colouring = nullptr;
+    sub.cuda_stream = c->stream;
+    if (sub.tile_width == 0) sub.tile_width = opt.precision == LD_MIXED ? 2 : 1;
+    c->T = sub.tile_width;
+    c->subs.reserve(count);
+    for (int i = 0; i < count; ++i) {
+        if (Qs[i].kind == LD_CSR) return fail(LD_EUNSUPPORTED, "batched instances are grid kinds");
+        ld_ctx *sc = nullptr;
+        ld_status st = ld_create(&Qs[i], distances[i], n_shifts, tol, &sub, &sc);
+        if (st != LD_OK) {
+            std::string msg = g_err;
+            return fail(st, "instance %d: %s", i, msg.c_str());
+        }
+        c->subs.push_back(sc);
+    }
+    // device table of the instances' solves and the work items, longest first
+    std::vector<Solve> solves(count);
+    std::vector<int> ncol(count);
+    struct Item { double cost; int inst, tile; };
+    std::vector<Item> items;
+    for (int i = 0; i < count; ++i) {
+        const ld_ctx *sc = c->subs[i];
+        solves[i] = sc->s;
+        ncol[i] = sc->ncolours;
+        const double cost = (double)sc->n * std::sqrt(sc->lmax / sc->lmin);
+        for (int t = 0; t < sc->ntiles; ++t) items.push_back({cost, i, t});
+    }
+    std::stable_sort(items.begin(), items.end(), [](const Item &x, const Item &y) { return x.cost > y.cost; });
+    std::vector<int2> hitems(items.size());
+    for (size_t k = 0; k < items.size(); ++k) hitems[k] = make_int2(items[k].inst, items[k].tile);
+    c->nitems = (int)items.size();
+    CUDA_TRY(c->d_solves.alloc(sizeof(Solve) * count));
+    CUDA_TRY(cudaMemcpy(c->d_solves.p, solves.data(), sizeof(Solve) * count, cudaMemcpyHostToDevice));
+    CUDA_TRY(c->d_items.alloc(sizeof(int2) * hitems.size()));
+    CUDA_TRY(cudaMemcpy(c->d_items.p, hitems.data(), sizeof(int2) * hitems.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(c->d_queue.alloc(sizeof(int)));
+    CUDA_TRY(c->d_bout.alloc(sizeof(double) * 2 * count));
+    CUDA_TRY(c->d_bint.alloc(sizeof(int) * 3 * count));
+    CUDA_TRY(cudaMemcpy(c->d_bint.as<int>() + 2 * count, ncol.data(), sizeof(int) * count, cudaMemcpyHostToDevice));
+    int dev = 0, sms = 152;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int occ = ld::engine_batch_occupancy(opt.precision == LD_MIXED ? 1 : 0, c->T);
+    c->bgrid = std::max(1, std::min(c->nitems, occ * sms));
+    // one CUDA graph: queue reset, per-instance prep, the persistent solve, per-instance sums
+    const int max_iter = opt.max_iter > 0 ? opt.max_iter : 100000;
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    const int err = ld::engine_batch(c->d_solves.as<Solve>(), c->d_bint.as<int>() + 2 * count, count,
+                                     c->d_items.as<int2>(), c->nitems, c->d_queue.as<int>(), max_iter,
+                                     opt.precision == LD_MIXED ? 1 : 0, c->T, c->bgrid,
+                                     c->d_bout.as<double>(), c->d_bout.as<double>() + count,
+                                     c->d_bint.as<int>(), c->d_bint.as<int>() + count, c->stream);
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (err) {
+        if (g) cudaGraphDestroy(g);
+        return fail(LD_ECUDA, "batch capture: %s", ld::engine_error_string(err));
+    }
+    if (e2 != cudaSuccess) return fail(LD_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e2));
+    cudaError_t e3 = cudaGraphInstantiate(&c->bgraph, g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess) {
+        c->bgraph = nullptr;
+        return fail(LD_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e3));
+    }
+    *out = guard.release();
+    return LD_OK;
 }
 
-ld_status ld_batch_logdet(ld_ctx *, double *, double *, ld_info *) {
-    return fail(LD_EUNSUPPORTED, "batched contexts are not available in this build");
+ld_status ld_batch_logdet(ld_ctx *c, double *logdets, double *grads, ld_info *info) {
+    if (!c || !logdets) return fail(LD_EINVAL, "ctx and logdets must be non-NULL");
+    if (!c->is_batch) return fail(LD_EINVAL, "not a batched context");
+    const int count = (int)c->subs.size();
+    std::vector<double> out(2 * count);
+    std::vector<int> flags(2 * count);
+    CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+    CUDA_TRY(cudaGraphLaunch(c->bgraph, c->stream));
+    CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(out.data(), c->d_bout.p, sizeof(double) * 2 * count, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(flags.data(), c->d_bint.p, sizeof(int) * 2 * count, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    int iters = 0;
+    ld_status st = LD_OK;
+    for (int i = 0; i < count; ++i) {
+        iters = std::max(iters, flags[count + i]);
+        const int f = flags[i];
+        if (f == 0 || st != LD_OK) continue;
+        if (f == ld::DEV_NOTSPD) st = fail(LD_ENOTSPD, "instance %d: Q is not SPD", i);
+        else if (f == -1) st = fail(LD_ENOTCONV, "instance %d: max_iter reached", i);
+        else st = fail(LD_ENUMERIC, "instance %d: non-finite CG scalar", i);
+    }
+    if (info) {
+        std::memset(info, 0, sizeof *info);
+        info->status = st;
+        info->n_shifts = c->nshift;
+        info->iters = iters;
+        info->tile_width = c->T;
+        info->engine = 2;
+        info->ms = ms;
+        info->iter_ms = ms;
+        info->gpu_launches = 3;
+        int64_t ti = 0;
+        for (int i = 0; i < count; ++i) ti += (int64_t)c->subs[i]->ntiles * flags[count + i];
+        info->tile_iters = ti;   // upper bound: every tile counted at its instance's iterations
+        info->n_colours = 0;
+        for (ld_ctx *sc : c->subs) info->n_colours += sc->ncolours;
+    }
+    if (st != LD_OK) return st;
+    for (int i = 0; i < count; ++i) {
+        logdets[i] = out[i];
+        if (grads) {
+            const ld_ctx *sc = c->subs[i];
+            const bool projected = (sc->kind == LD_STENCIL_2D5 || sc->kind == LD_STENCIL_3D7) && !sc->has_field;
+            grads[i] = projected ? sc->scale * out[count + i] : std::nan("");
+        }
+    }
+    return LD_OK;
 }
 
 void ld_destroy(ld_ctx *c) { delete c; }

@@ -611,7 +611,7 @@ struct Strip {
 // threads per lattice column: one thread holds all T columns of its lattice
 // column, so per-row address, loop and barrier work is shared by T columns
 template <typename V, int T>
-constexpr int stream_groups() {
+__host__ __device__ constexpr int stream_groups() {
     return 1;
 }
 
@@ -762,7 +762,7 @@ __device__ __forceinline__ Pack<V, TS> diff5(V c, const Pack<V, TS> &pc, const P
 // resident CTAs per SM the register budget is sized for
 constexpr int stream_min_blocks(int G) { return G == 1 ? 3 : 2; }
 template <typename V, int T>
-constexpr int stream_min_blocks_t() { return sizeof(V) * T <= 8 ? 6 : (sizeof(V) * T <= 16 ? 4 : 3); }
+__host__ __device__ constexpr int stream_min_blocks_t() { return sizeof(V) * T <= 8 ? 6 : (sizeof(V) * T <= 16 ? 4 : 3); }
 
 constexpr int STREAM_PD = 6;   // ring depth: rows held per thread (cp.async)
 
@@ -776,17 +776,31 @@ constexpr size_t stream_smem_bytes() {
     return rows > part ? (rows > red ? rows : red) : (part > red ? part : red);
 }
 
+// per-thread dot accumulators of a streaming sweep (TS columns of the thread)
+template <typename V, int TS>
+struct StreamAcc {
+    Pack<V, TS> rr, pw, rw, ww;
+    V vr[TS], vw[TS];
+    __device__ __forceinline__ void zero() {
+        rr = pw = rw = ww = zero_pack<V, TS>();
+#pragma unroll
+        for (int t = 0; t < TS; ++t) vr[t] = vw[t] = (V)0;
+    }
+};
+
+// One CTA sweeps lattice strip `strip`, rows [ys, ye), of one tile: the fused pass
+// for those vertices, dot products accumulated into acc.  smem: stream_smem_bytes.
+// Returns with no copy in flight and shared memory free (after a barrier).
 template <typename V, int T, int G, int KIND, bool KEEPX>
-__global__ void __launch_bounds__(SW * G, stream_min_blocks_t<V, T>()) k_stream2d(Solve s, int cur) {
-    constexpr int TS = T / G, H = Strip<KIND>::H, K = NDOT * T, PD = STREAM_PD;
+__device__ __forceinline__ void stream_sweep(const Solve &s, int tile, int cur, int strip, int ys,
+                                             int ye, unsigned char *smem,
+                                             StreamAcc<V, T / G> &acc) {
+    constexpr int TS = T / G, H = Strip<KIND>::H, PD = STREAM_PD;
     constexpr int NT = SW * G;          // threads; also the pack count of one shared row
     using P = Pack<V, TS>;
-    const int tile = blockIdx.y;
-    if (s.tile_done[tile]) return;
-    // shared: [ps: 2 rows | us: 2 rows | ring: PD x (r, w, p) rows]; the ring is
-    // per-thread private (each thread copies and reads back only its own packs), so
-    // it needs no barrier.  After the row loop the bytes hold the partial sums.
-    extern __shared__ __align__(16) unsigned char smem[];
+    // shared: [ps: 2 rows | us: 2 rows | ring: PD x (r, w, p) rows + colours]; the ring
+    // is per-thread private (each thread copies and reads back only its own packs), so
+    // it needs no barrier.
     P *const ps = reinterpret_cast<P *>(smem);
     P *const us = ps + 2 * NT;
     P *const ring = ps + 4 * NT + threadIdx.x;
@@ -794,12 +808,10 @@ __global__ void __launch_bounds__(SW * G, stream_min_blocks_t<V, T>()) k_stream2
     const int nx = s.op.nx, ny = s.op.ny;
     const bool per = s.op.periodic;
     const int xl = threadIdx.x / G, g = threadIdx.x - xl * G;
-    const int strip = blockIdx.x % s.strips, sg = blockIdx.x / s.strips;
     const int gx = strip * Strip<KIND>::W - H + xl;
     bool inx;
     const int gxw = wrap_coord(gx, nx, per, inx);
     const bool outx = xl >= H && xl < H + Strip<KIND>::W && gx < nx;
-    const int ys = sg * s.seg, ye = min(ys + s.seg, ny);
     const int cb = tile * T + g * TS;
     const int64_t off = (int64_t)tile * s.op.n * T + g * TS;
     const V *const r = static_cast<const V *>(cur ? s.rbuf[1] : s.rbuf[0]) + off;
@@ -807,15 +819,11 @@ __global__ void __launch_bounds__(SW * G, stream_min_blocks_t<V, T>()) k_stream2
     const V *const p = static_cast<const V *>(cur ? s.pbuf[1] : s.pbuf[0]) + off;
     using M = PackMath<V, TS>;
     P na, b;                  // -alpha, beta per column
-    P d_rr, d_pw, d_rw, d_ww; // dot accumulators
-    V d_vr[TS], d_vw[TS];
 #pragma unroll
     for (int t = 0; t < TS; ++t) {
         na.v[t] = -(V)s.alpha[cb + t];
         b.v[t] = (V)s.beta[cb + t];
-        d_vr[t] = d_vw[t] = (V)0;
     }
-    d_rr = d_pw = d_rw = d_ww = zero_pack<V, TS>();
     P pw0 = zero_pack<V, TS>(), pw1 = pw0, pw2 = pw0;   // p at rows y-2, y-1, y
     P uw0 = pw0, uw1 = pw0, uw2 = pw0;                   // u at rows y-3, y-2, y-1
 
@@ -856,15 +864,15 @@ __global__ void __launch_bounds__(SW * G, stream_min_blocks_t<V, T>()) k_stream2
             *reinterpret_cast<P *>(x + e) = M::fma(M::neg(na), q[2 * NT], xo);
         }
         const int lc = ringc[slot * NT] - cb;
-        d_rr = M::fma(rk, rk, d_rr);
-        d_pw = M::fma(pk, wk, d_pw);
-        d_rw = M::fma(rk, wk, d_rw);
-        d_ww = M::fma(wk, wk, d_ww);
+        acc.rr = M::fma(rk, rk, acc.rr);
+        acc.pw = M::fma(pk, wk, acc.pw);
+        acc.rw = M::fma(rk, wk, acc.rw);
+        acc.ww = M::fma(wk, wk, acc.ww);
 #pragma unroll
         for (int t = 0; t < TS; ++t) {
             if (lc == t) {
-                d_vr[t] += rk.v[t];
-                d_vw[t] += wk.v[t];
+                acc.vr[t] += rk.v[t];
+                acc.vw[t] += wk.v[t];
             }
         }
     };
@@ -929,31 +937,52 @@ __global__ void __launch_bounds__(SW * G, stream_min_blocks_t<V, T>()) k_stream2
     }
     cp_async_wait<0>();
     __syncthreads();
-    // CTA sums: per-thread partials -> shared, then one thread per (dot, column)
-    // adds the partials of its SW lattice columns in a fixed order (FP64)
+}
+
+// CTA sums of the sweep accumulators into cta[NDOT*T] (shared): per-thread partials,
+// then one thread per (dot, column) adds its SW lattice columns in a fixed order.
+// smem: >= SW*G*NDOT*TS words of V.  Ends with a barrier.
+template <typename V, int T, int G>
+__device__ __forceinline__ void stream_cta_sums(const StreamAcc<V, T / G> &acc, unsigned char *smem,
+                                                double *cta) {
+    constexpr int TS = T / G, K = NDOT * T;
     V *part = reinterpret_cast<V *>(smem);
     {
         V *mine = part + threadIdx.x * NDOT * TS;
 #pragma unroll
         for (int t = 0; t < TS; ++t) {
-            mine[0 * TS + t] = d_rr.v[t];
-            mine[1 * TS + t] = d_pw.v[t];
-            mine[2 * TS + t] = d_rw.v[t];
-            mine[3 * TS + t] = d_ww.v[t];
-            mine[4 * TS + t] = d_vr[t];
-            mine[5 * TS + t] = d_vw[t];
+            mine[0 * TS + t] = acc.rr.v[t];
+            mine[1 * TS + t] = acc.pw.v[t];
+            mine[2 * TS + t] = acc.rw.v[t];
+            mine[3 * TS + t] = acc.ww.v[t];
+            mine[4 * TS + t] = acc.vr[t];
+            mine[5 * TS + t] = acc.vw[t];
         }
     }
     __syncthreads();
-    __shared__ double cta[K];
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         const int dot = k / T, col = k - dot * T;
         const int gg = col / TS, t = col - gg * TS;
-        double acc = 0.0;
-        for (int xx = 0; xx < SW; ++xx) acc += (double)part[(xx * G + gg) * NDOT * TS + dot * TS + t];
-        cta[k] = acc;
+        double a = 0.0;
+        for (int xx = 0; xx < SW; ++xx) a += (double)part[(xx * G + gg) * NDOT * TS + dot * TS + t];
+        cta[k] = a;
     }
     __syncthreads();
+}
+
+template <typename V, int T, int G, int KIND, bool KEEPX>
+__global__ void __launch_bounds__(SW * G, stream_min_blocks_t<V, T>()) k_stream2d(Solve s, int cur) {
+    constexpr int K = NDOT * T;
+    const int tile = blockIdx.y;
+    if (s.tile_done[tile]) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int strip = blockIdx.x % s.strips, sg = blockIdx.x / s.strips;
+    const int ys = sg * s.seg, ye = min(ys + s.seg, s.op.ny);
+    StreamAcc<V, T / G> acc;
+    acc.zero();
+    stream_sweep<V, T, G, KIND, KEEPX>(s, tile, cur, strip, ys, ye, smem, acc);
+    __shared__ double cta[K];
+    stream_cta_sums<V, T, G>(acc, smem, cta);
     publish_and_tail<K>(s, tile, cur, cta, reinterpret_cast<double *>(smem));
 }
 
@@ -983,6 +1012,201 @@ __global__ void __launch_bounds__(256) k_cta_solve(Solve s, int max_iter) {
         __syncthreads();
     }
 }
+
+// ------------------------------------------------------------------ batched engine
+// Many independent problems (one Solve each, in device memory) in one
+// persistent launch: CTAs pull (instance, tile) items from an atomic queue
+// (the host sorts items longest first), initialise the tile's state and run
+// its whole solve with block barriers, exactly as the one-CTA engine does.
+
+// tile state as the init kernels set it (all colours of the instance active)
+template <typename V, int T>
+__device__ void tile_init(const Solve &s, int tile) {
+    const int64_t n = s.op.n;
+    const int64_t off = (int64_t)tile * n * T;
+    V *r = static_cast<V *>(s.rbuf[0]) + off;
+    V *w = static_cast<V *>(s.wbuf[0]) + off;
+    V *p = static_cast<V *>(s.pbuf[0]) + off;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const int lc = s.colour[i] - tile * T;
+        V a[T], z[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            a[t] = (lc == t && s.class_size[tile * T + t] > 0.0) ? (V)1 : (V)0;
+            z[t] = (V)0;
+        }
+        stpack<V, T>(r, i, a);
+        stpack<V, T>(w, i, z);
+        stpack<V, T>(p, i, z);
+    }
+    const int N = s.nshift;
+    for (int q = threadIdx.x; q < T * N; q += blockDim.x) {
+        const int c = tile * T + q / N;
+        const double vv = s.class_size[c];
+        const int idx = c * N + (q % N);
+        s.zeta[idx] = make_double2(1.0, 0.0);
+        s.zeta_prev[idx] = make_double2(1.0, 0.0);
+        s.pi[idx] = make_double2(0.0, 0.0);
+        s.phi[idx] = make_double2(vv, 0.0);
+        s.sh_active[idx] = (uint8_t)(vv > 0.0);
+    }
+    if (threadIdx.x < T) {
+        const int c = tile * T + threadIdx.x;
+        const double vv = s.class_size[c];
+        s.rho[c] = vv;
+        s.vnorm2[c] = vv;
+        s.alpha[c] = 0.0;
+        s.beta[c] = 0.0;
+        s.alpha_prev[c] = 1.0;
+        s.beta_prev[c] = 0.0;
+        s.pi0[c] = 0.0;
+        s.phi0[c] = vv;
+        s.col_active[c] = vv > 0.0;
+        s.col_iters[c] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int any = 0;
+        for (int t = 0; t < T; ++t) any |= s.col_active[tile * T + t];
+        s.tile_done[tile] = !any;
+        s.tile_ctr[tile] = 0;
+        s.tile_par[tile] = 0;
+    }
+    __syncthreads();
+}
+
+// A tile's whole solve in the calling CTA (block barriers only).
+template <typename V, int T, int KIND>
+__device__ void tile_solve(const Solve &s, int tile, int max_iter, double *red, double *sums,
+                           int *done) {
+    constexpr int K = NDOT * T;
+    if (threadIdx.x == 0) *done = s.tile_done[tile];
+    __syncthreads();
+    for (int it = 0; it < max_iter && !*done; ++it) {
+        const int cur = it & 1;
+        Dots<V, T> d;
+        d.zero();
+        pass_points<V, T, KIND, false>(s, tile, cur, threadIdx.x, blockDim.x, d);
+        V flat[K];
+        d.flat(flat);
+        block_sum_to<V, K>(flat, red, sums);
+        fused_tail(s, tile, cur, sums);
+        __syncthreads();
+        if (threadIdx.x == 0) *done = s.tile_done[tile] || (*s.status != 0);
+        __syncthreads();
+    }
+}
+
+// The persistent batch kernel: 2D lattice instances run the streaming sweep (the
+// CTA walks every strip of its tile, all rows, per pass), the other kinds the
+// gather pass; either way one CTA owns the tile's whole solve.
+template <typename V, int T>
+__global__ void __launch_bounds__(SW * stream_groups<V, T>(), stream_min_blocks_t<V, T>())
+    k_batch_solve(const Solve *solves, const int2 *items, int nitems, int *queue, int max_iter) {
+    constexpr int K = NDOT * T, G = stream_groups<V, T>(), NW = SW * G / 32;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double red[NW * K];
+    __shared__ double sums[K];
+    __shared__ int done, item;
+    for (;;) {
+        if (threadIdx.x == 0) item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int my = item;
+        if (my >= nitems) break;
+        const int2 it = items[my];
+        const Solve &s = solves[it.x];
+        const int tile = it.y;
+        tile_init<V, T>(s, tile);
+        const int kind = s.op.kind;
+        if (kind == KIND_2D5 || kind == KIND_2D13_SQ) {
+            const int W = kind == KIND_2D13_SQ ? Strip<KIND_2D13_SQ>::W : Strip<KIND_2D5>::W;
+            const int strips = (s.op.nx + W - 1) / W;
+            if (threadIdx.x == 0) done = s.tile_done[tile];
+            __syncthreads();
+            for (int pass = 0; pass < max_iter && !done; ++pass) {
+                const int cur = pass & 1;
+                StreamAcc<V, T / G> acc;
+                acc.zero();
+                for (int st = 0; st < strips; ++st) {
+                    if (kind == KIND_2D13_SQ)
+                        stream_sweep<V, T, G, KIND_2D13_SQ, false>(s, tile, cur, st, 0, s.op.ny, smem, acc);
+                    else
+                        stream_sweep<V, T, G, KIND_2D5, false>(s, tile, cur, st, 0, s.op.ny, smem, acc);
+                }
+                stream_cta_sums<V, T, G>(acc, smem, sums);
+                fused_tail(s, tile, cur, sums);
+                __syncthreads();
+                if (threadIdx.x == 0) done = s.tile_done[tile] || (*s.status != 0);
+                __syncthreads();
+            }
+        } else if (kind == KIND_3D7) {
+            tile_solve<V, T, KIND_3D7>(s, tile, max_iter, red, sums, &done);
+        } else {
+            tile_solve<V, T, KIND_CSR>(s, tile, max_iter, red, sums, &done);
+        }
+        // per-column terms Re sum_l alpha_l pi_{c,l}
+        if (threadIdx.x < T) {
+            const int c = tile * T + threadIdx.x;
+            double acc = 0.0;
+            for (int l = 0; l < s.nshift; ++l) {
+                const double2 w = s.weight[l], p = s.pi[c * s.nshift + l];
+                acc += w.x * p.x - w.y * p.y;
+            }
+            s.terms[c] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// per instance: remaining tiles and status before the solve
+__global__ void k_batch_prep(const Solve *solves, int count) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        *solves[i].remaining = solves[i].ntiles;
+        *solves[i].status = 0;
+    }
+}
+
+// per instance (fixed column order): log det, the projected seed sum, convergence flag
+__global__ void k_batch_finish(const Solve *solves, const int *ncolours, int count, double *logdet,
+                               double *seed, int *flag, int *iters) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+        const Solve &s = solves[i];
+        double a = 0.0, b = 0.0;
+        int it = 0;
+        for (int c = 0; c < ncolours[i]; ++c) {
+            a += s.terms[c];
+            b += s.pi0[c];
+            it = max(it, s.col_iters[c]);
+        }
+        logdet[i] = a;
+        seed[i] = b;
+        iters[i] = it;
+        flag[i] = *s.status != 0 ? *s.status : (*s.remaining > 0 ? -1 : 0);
+    }
+}
+
+template <typename V, int T, int KIND>
+struct BatchLauncher {
+    static int run(const Solve *solves, const int2 *items, int nitems, int *queue, int max_iter,
+                   int grid, cudaStream_t st) {
+        constexpr int G = stream_groups<V, T>();
+        k_batch_solve<V, T><<<grid, SW * G, stream_smem_bytes<V, T, G>(), st>>>(solves, items, nitems,
+                                                                              queue, max_iter);
+        return (int)cudaGetLastError();
+    }
+};
+
+template <typename V, int T, int KIND>
+struct BatchOcc {
+    static int run(int *out) {
+        constexpr int G = stream_groups<V, T>();
+        constexpr size_t sm = stream_smem_bytes<V, T, G>();
+        cudaError_t e = cudaFuncSetAttribute(k_batch_solve<V, T>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return (int)e;
+        return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_batch_solve<V, T>, SW * G, sm);
+    }
+};
 
 // ------------------------------------------------------------------ init / flush / finish
 template <typename V, int T>
@@ -1381,6 +1605,28 @@ int engine_iteration(const Solve &s, int parity, void *stream) {
 int engine_cta_solve(const Solve &s, int max_iter, void *stream) {
     return dispatch<CtaLauncher>(s.precision, s.T, s.op.kind, s, max_iter,
                                  static_cast<cudaStream_t>(stream));
+}
+
+int engine_batch_occupancy(int precision, int T) {
+    int occ = 0;
+    if (dispatch<BatchOcc>(precision, T, KIND_2D5, &occ) != 0 || occ < 1) return 1;
+    return occ;
+}
+
+int engine_batch(const Solve *solves_dev, const int *ncolours_dev, int count, const int2 *items_dev,
+                 int nitems, int *queue_dev, int max_iter, int precision, int T, int grid,
+                 double *logdet_dev, double *seed_dev, int *flag_dev, int *iters_dev, void *stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int e = (int)cudaMemsetAsync(queue_dev, 0, sizeof(int), st);
+    if (e) return e;
+    k_batch_prep<<<(count + 255) / 256, 256, 0, st>>>(solves_dev, count);
+    if ((e = (int)cudaGetLastError())) return e;
+    e = dispatch<BatchLauncher>(precision, T, KIND_2D5, solves_dev, items_dev, nitems, queue_dev,
+                                max_iter, grid, st);
+    if (e) return e;
+    k_batch_finish<<<(count + 127) / 128, 128, 0, st>>>(solves_dev, ncolours_dev, count, logdet_dev,
+                                                       seed_dev, flag_dev, iters_dev);
+    return (int)cudaGetLastError();
 }
 
 int engine_flush_x(const Solve &s, void *stream) {

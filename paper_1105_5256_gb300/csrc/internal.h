@@ -91,6 +91,11 @@ int engine_init(const Solve &s, int col_begin, int col_end, void *stream);
 int engine_iteration(const Solve &s, int parity, void *stream);      // one fused CG pass
 int engine_cta_solve(const Solve &s, int max_iter, void *stream);    // whole solve, one CTA per tile
 int engine_flush_x(const Solve &s, void *stream);                    // last seed-solution update
+// batched engine: all instances' tiles in one persistent launch (plus prep/finish)
+int engine_batch_occupancy(int precision, int T);
+int engine_batch(const Solve *solves_dev, const int *ncolours_dev, int count, const int2 *items_dev,
+                 int nitems, int *queue_dev, int max_iter, int precision, int T, int grid,
+                 double *logdet_dev, double *seed_dev, int *flag_dev, int *iters_dev, void *stream);
 int engine_finish(const Solve &s, int col_begin, int col_end, void *stream);
 int engine_apply(const Operator &op, int precision, int T, int ntiles, const void *x, void *y,
                  void *stream);
