@@ -107,6 +107,23 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_draws(rank: int, count: int):
+    """kappa^2 draws of one rank: an independent seeded batch per rank (weak scaling)."""
+    return synth.kappa2_draws(SEED + 1000 * rank, count)
+
+
+def colour_ranges(n_colours: int, world: int):
+    """Contiguous colour ranges [a, b) splitting one evaluation over `world` ranks
+    (sizes differ by at most one); partial log dets of the ranges add up."""
+    base, extra = divmod(n_colours, world)
+    out, a = [], 0
+    for r in range(world):
+        b = a + base + (1 if r < extra else 0)
+        out.append((a, b))
+        a = b
+    return out
+
+
 def algorithmic_bytes(n, T, prec, tile_iters, passes):
     """Algorithmic HBM bytes of the CG passes of a solve.
 
@@ -184,7 +201,7 @@ def run_ours(args):
         torch.cuda.set_device(0)
     L.library(build_if_missing=True)
     prec = L.LD_MIXED if args.precision == "mixed" else L.LD_FP64
-    draws = synth.kappa2_draws(SEED + 1000 * rank, args.batch)
+    draws = rank_draws(rank, args.batch)
     if args.kappa2 > 0:
         draws = np.full(args.batch, args.kappa2)
     ctx = L.ld_create(L.grid_matrix(L.LD_STENCIL_2D13_SQ, DIMS, float(draws[0])), DIST, NSHIFT,

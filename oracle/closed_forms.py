@@ -68,11 +68,12 @@ def spectral_coeffs(grid_vals: np.ndarray, periodic: bool) -> np.ndarray:
 
 
 def probed_value(kind, dims, kappa2, periodic, colour: np.ndarray, f, scale=1.0,
-                 per_colour: bool = False):
+                 per_colour: bool = False, colours=None):
     """sum_c v_c^T f(Q) v_c with v_c = indicator(colour == c).
 
     f maps an eigenvalue array to values (real).  Returns the total, or the
-    per-colour array when per_colour=True.
+    per-colour array when per_colour=True.  `colours` restricts the classes
+    evaluated (the others are left at zero), for sampled checks of large grids.
     """
     dims = [int(d) for d in dims]
     shape = tuple(reversed(dims))
@@ -81,7 +82,7 @@ def probed_value(kind, dims, kappa2, periodic, colour: np.ndarray, f, scale=1.0,
     col = np.asarray(colour).reshape(shape)
     ncol = int(col.max()) + 1 if col.size else 0
     out = np.zeros(ncol)
-    for c in range(ncol):
+    for c in (range(ncol) if colours is None else colours):
         v = (col == c).astype(np.float64)
         out[c] = float(np.sum(flam * spectral_coeffs(v, periodic)))
     return out if per_colour else float(out.sum())

@@ -1,0 +1,73 @@
+"""Multi-process (world size 2, gloo, CPU) checks of the sharding logic.
+
+The path shards by independent problems (each rank evaluates its own seeded
+kappa^2 batch, no data-path collective) or, for one evaluation, by colour ranges
+whose partial sums add up (the paper's one-probing-vector-per-node scheme,
+Sec. 2.1).  These tests run the host-side logic in two gloo processes.
+"""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import torch
+    draws = bench.rank_draws(rank, 16)
+    got = [None] * world
+    dist.all_gather_object(got, [float(x) for x in draws])
+    # colour ranges of one evaluation split across ranks
+    ranges = bench.colour_ranges(18, world)
+    gathered = [None] * world
+    dist.all_gather_object(gathered, ranges[rank])
+    # max-over-ranks timing
+    t = torch.tensor([1.0 + rank], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    if rank == 0:
+        q.put((got, gathered, float(t[0])))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_sharding_and_timing():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    got, gathered, tmax = q.get(timeout=120)
+    for p in ps:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert got[0] != got[1]                       # independent seeded batches
+    assert np.allclose(got[0], bench.rank_draws(0, 16))
+    cover = sorted(c for a, b in gathered for c in range(a, b))
+    assert cover == list(range(18))               # colour ranges partition [0, C)
+    assert tmax == 2.0                            # the slowest rank sets the time
+
+
+def test_colour_ranges_cover_and_balance():
+    for C in (1, 5, 18, 107):
+        for world in (1, 2, 3, 8):
+            rs = bench.colour_ranges(C, world)
+            assert len(rs) == world
+            assert rs[0][0] == 0 and rs[-1][1] == C
+            assert all(a <= b for a, b in rs)
+            assert all(rs[k][1] == rs[k + 1][0] for k in range(world - 1))
+            sizes = [b - a for a, b in rs]
+            assert max(sizes) - min(sizes) <= 1
