@@ -178,6 +178,14 @@ ld_status ld_get_nodes(const ld_ctx *ctx, double *sigma, double *alpha, int32_t 
  * context's precision. */
 ld_status ld_apply(ld_ctx *ctx, int ncols, const double *x, double *y);
 
+/* y_j ~ log(Q) v_j = Re sum_l alpha_l (Q - sigma_l I)^{-1} v_j for arbitrary right-hand
+ * sides (Sec. 2.1, Eq. "eq_rat_app"), by the vector form of CG-M: the seed CG on Q x = v_j
+ * plus one complex search direction per shift, accumulating y directly.  V, Y host arrays,
+ * row-major n x ncols, FP64 (the vectors run in the context's precision).  Uses the
+ * context's operator, nodes and tolerance; needs about (6 w + 16 N + 8) n ncols bytes of
+ * device memory for the call.  Errors as ld_logdet. */
+ld_status ld_logmv(ld_ctx *ctx, int ncols, const double *V, double *Y, ld_info *info);
+
 /* Host utilities (no device work; usable without a GPU). */
 
 /* Greedy distance-d colouring of the CSR pattern in natural order (Sec. 2.1).

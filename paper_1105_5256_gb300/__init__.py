@@ -93,6 +93,7 @@ def library(build_if_missing: bool = False):
         "ld_get_colouring": ([vp, vp, P(i32)], st),
         "ld_get_nodes": ([vp, vp, vp, P(i32)], st),
         "ld_apply": ([vp, C.c_int, vp, vp], st),
+        "ld_logmv": ([vp, C.c_int, vp, vp, P(Info)], st),
         "ld_colour_csr": ([i64, vp, vp, C.c_int, vp, P(i32)], st),
         "ld_colour_grid": ([C.c_int, vp, C.c_int, C.c_int, vp, P(i32)], st),
         "ld_hht_nodes": ([dbl, dbl, C.c_int, vp, vp, P(dbl)], st),
@@ -277,6 +278,17 @@ def ld_apply(ctx: Context, x: np.ndarray) -> np.ndarray:
     y = np.zeros_like(x)
     _check(library().ld_apply(ctx.handle, x.shape[1], _ptr(x), _ptr(y)))
     return y
+
+
+def ld_logmv(ctx: Context, V: np.ndarray):
+    """log(Q) V for an n x k block (vector form of CG-M); returns (Y, info)."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    if V.ndim == 1:
+        V = V[:, None]
+    Y = np.zeros_like(V)
+    info = Info()
+    _check(library().ld_logmv(ctx.handle, V.shape[1], _ptr(V), _ptr(Y), C.byref(info)))
+    return Y, info.as_dict()
 
 
 def ld_colour_csr(rowptr, colidx, d: int):

@@ -9,9 +9,14 @@
 #include <complex>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <new>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -420,6 +425,108 @@ ld_status run_solve(ld_ctx *c, int cb, int ce, bool keep_x0, double out[2], ld_i
     return st;
 }
 
+// ---------------------------------------------------------------- tile-width autotuner
+// For large grid-engine problems created with tile_width = 0, a few CG passes are
+// timed for every candidate tile width (trial contexts sharing the colouring) and
+// the fastest is kept, per (kind, precision, boundary, dims, colours).  Results are
+// cached for the process and, when LD_AUTOTUNE_CACHE names a file, in that JSON
+// file ({"key": tile_width, ...}).
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_key(const ld_matrix *Q, int precision, int ncolours) {
+    std::ostringstream k;
+    k << Q->kind << ":" << precision << ":" << (Q->periodic ? 1 : 0) << ":" << Q->dims[0] << "x"
+      << Q->dims[1] << "x" << (Q->kind == LD_STENCIL_3D7 ? Q->dims[2] : 1) << ":" << ncolours
+      << (Q->kappa2_field ? ":field" : "") << (Q->obs_mask ? ":mask" : "");
+    return k.str();
+}
+
+void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = std::getenv("LD_AUTOTUNE_CACHE");
+    if (!path) return;
+    std::ifstream f(path);
+    if (!f) return;
+    std::stringstream ss;
+    ss << f.rdbuf();
+    const std::string s = ss.str();
+    size_t pos = 0;
+    while ((pos = s.find('"', pos)) != std::string::npos) {
+        const size_t end = s.find('"', pos + 1);
+        if (end == std::string::npos) break;
+        const std::string key = s.substr(pos + 1, end - pos - 1);
+        const size_t colon = s.find(':', end);
+        if (colon == std::string::npos) break;
+        const int t = std::atoi(s.c_str() + colon + 1);
+        if (t > 0) g_tune[key] = t;
+        pos = s.find_first_of(",}", colon);
+        if (pos == std::string::npos) break;
+    }
+}
+
+void tune_save_locked() {
+    const char *path = std::getenv("LD_AUTOTUNE_CACHE");
+    if (!path) return;
+    std::ofstream f(path);
+    f << "{";
+    bool first = true;
+    for (const auto &kv : g_tune) {
+        f << (first ? "" : ", ") << "\"" << kv.first << "\": " << kv.second;
+        first = false;
+    }
+    f << "}\n";
+}
+
+int autotune_tile(const ld_matrix *Q, int d, int N, double tol, const ld_options &opt,
+                  const std::vector<int32_t> &colour, int ncolours) {
+    const std::string key = tune_key(Q, opt.precision, ncolours);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        tune_load_locked();
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) return it->second;
+    }
+    static const int f64[4] = {1, 2, 3, 4};
+    static const int f32[4] = {2, 4, 6, 8};
+    const int *cand = opt.precision == LD_FP64 ? f64 : f32;
+    int best = -1;
+    double best_ms = 1e300;
+    for (int k = 0; k < 4; ++k) {
+        const int T = cand[k];
+        const int cols = (ncolours + T - 1) / T * T;
+        if (8 * (cols - ncolours) > ncolours) continue;   // more than 1/8 padding
+        ld_options sub = opt;
+        sub.tile_width = T;
+        sub.colouring = colour.data();
+        sub.max_iter = 16;
+        sub.chunk_iters = 8;
+        sub.engine = 1;
+        sub.keep_x0 = 0;
+        ld_ctx *t = nullptr;
+        if (ld_create(Q, d, N, tol, &sub, &t) != LD_OK) continue;
+        double v;
+        ld_info info{};
+        ld_logdet(t, &v, &info);   // usually LD_ENOTCONV after 16 passes: only the timing matters
+        ld_destroy(t);
+        if (info.iters < 1 || !(info.iter_ms > 0.0)) continue;
+        const double per_pass = info.iter_ms / info.iters;
+        if (per_pass < best_ms) {
+            best_ms = per_pass;
+            best = T;
+        }
+    }
+    g_err = "no error";
+    if (best > 0) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune[key] = best;
+        tune_save_locked();
+    }
+    return best;
+}
+
 ld_status check_params(const ld_ctx *c, int n_params, const int *ids) {
     if (n_params < 1 || n_params > 3 || !ids) return fail(LD_EINVAL, "n_params must be 1..3 with ids");
     for (int k = 0; k < n_params; ++k) {
@@ -506,8 +613,11 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
     } else {
         c->ncolours = ld::colour_grid(c->kind, c->dims, c->periodic, colouring_distance, c->colour.data());
     }
-    // tiling
-    c->T = choose_tile(opt.precision, c->ncolours, opt.tile_width);
+    // tiling: explicit, autotuned (large multi-CTA problems), or the padding rule
+    c->T = -1;
+    if (opt.tile_width == 0 && opt.engine != 2 && c->n >= 65536 && c->kind != LD_CSR)
+        c->T = autotune_tile(Q, colouring_distance, n_shifts, tol, opt, c->colour, c->ncolours);
+    if (c->T < 0) c->T = choose_tile(opt.precision, c->ncolours, opt.tile_width);
     if (c->T < 0) return fail(LD_EINVAL, "tile_width %d not available for this precision", opt.tile_width);
     c->ntiles = (c->ncolours + c->T - 1) / c->T;
     c->ncols = c->ntiles * c->T;
@@ -787,6 +897,110 @@ ld_status ld_apply(ld_ctx *c, int ncols, const double *x, double *y) {
                 const size_t q = ((size_t)t * n + i) * T + k;
                 y[i * ncols + col] = f32 ? (double)reinterpret_cast<float *>(hy.data())[q]
                                          : reinterpret_cast<double *>(hy.data())[q];
+            }
+    return LD_OK;
+}
+
+ld_status ld_logmv(ld_ctx *c, int ncols, const double *V, double *Y, ld_info *info) {
+    if (!c || !V || !Y || ncols < 1) return fail(LD_EINVAL, "bad arguments");
+    if (c->is_batch) return fail(LD_EINVAL, "batched context");
+    const int T = c->T, N = c->nshift;
+    const int nt = (ncols + T - 1) / T, C = nt * T;
+    const int64_t n = c->n;
+    const bool f32 = c->opt.precision == LD_MIXED;
+    const size_t w = f32 ? 4 : 8;
+    const size_t elems = (size_t)nt * n * T;
+    // host: right-hand sides in the tiled layout, their squared norms
+    std::vector<unsigned char> hv(elems * w, 0);
+    std::vector<double> norm2(C, 0.0);
+    for (int t = 0; t < nt; ++t)
+        for (int64_t i = 0; i < n; ++i)
+            for (int k = 0; k < T; ++k) {
+                const int col = t * T + k;
+                const double v = col < ncols ? V[i * ncols + col] : 0.0;
+                const size_t q = ((size_t)t * n + i) * T + k;
+                if (f32) reinterpret_cast<float *>(hv.data())[q] = (float)v;
+                else reinterpret_cast<double *>(hv.data())[q] = v;
+                norm2[col] += v * v;
+            }
+    DevBuf vec[6], cs, ci, sh, sig, tl, part, tm, psig, y;
+    for (auto &b : vec) CUDA_TRY(b.alloc(elems * w));
+    CUDA_TRY(cs.alloc((size_t)8 * C * sizeof(double)));
+    CUDA_TRY(ci.alloc((size_t)2 * C * sizeof(int32_t)));
+    CUDA_TRY(sh.alloc((size_t)4 * C * N * sizeof(double2) + (size_t)C * N));
+    CUDA_TRY(sig.alloc((size_t)2 * C * N * sizeof(double2)));
+    CUDA_TRY(tl.alloc((size_t)(3 * nt + 2) * sizeof(int32_t)));
+    CUDA_TRY(tm.alloc((size_t)(2 * C + 8) * sizeof(double)));
+    CUDA_TRY(psig.alloc((size_t)C * N * n * sizeof(double2)));
+    CUDA_TRY(y.alloc(elems * sizeof(double)));
+    Solve s = c->s;
+    s.T = T;
+    s.ntiles = nt;
+    s.ncols = C;
+    s.keep_x0 = 0;
+    s.x = nullptr;
+    for (int k = 0; k < 2; ++k) {
+        s.rbuf[k] = vec[k].p;
+        s.wbuf[k] = vec[2 + k].p;
+        s.pbuf[k] = vec[4 + k].p;
+    }
+    double *d = cs.as<double>();
+    s.rho = d; s.alpha = d + C; s.beta = d + 2 * C; s.alpha_prev = d + 3 * C;
+    s.beta_prev = d + 4 * C; s.vnorm2 = d + 5 * C; s.pi0 = d + 6 * C; s.phi0 = d + 7 * C;
+    s.col_active = ci.as<int32_t>();
+    s.col_iters = s.col_active + C;
+    double2 *z = sh.as<double2>();
+    s.zeta = z; s.zeta_prev = z + (size_t)C * N; s.pi = z + (size_t)2 * C * N; s.phi = z + (size_t)3 * C * N;
+    s.sh_active = reinterpret_cast<uint8_t *>(z + (size_t)4 * C * N);
+    s.asig = sig.as<double2>();
+    s.bsig = s.asig + (size_t)C * N;
+    s.tile_done = tl.as<int32_t>(); s.tile_ctr = s.tile_done + nt; s.tile_par = s.tile_ctr + nt;
+    s.remaining = s.tile_par + nt; s.status = s.remaining + 1;
+    s.terms = tm.as<double>(); s.class_size = s.terms + C; s.result = s.terms + 2 * C;
+    ld::engine_plan(s);
+    CUDA_TRY(part.alloc(std::max<size_t>((size_t)nt * s.bpt * ld::NDOT * T, 1824) * sizeof(double)));
+    s.partial = part.as<double>();
+    CUDA_TRY(cudaMemsetAsync(tl.p, 0, tl.bytes, c->stream));
+    CUDA_TRY(cudaMemsetAsync(sig.p, 0, sig.bytes, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(vec[0].p, hv.data(), elems * w, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemsetAsync(vec[2].p, 0, elems * w, c->stream));
+    CUDA_TRY(cudaMemsetAsync(vec[4].p, 0, elems * w, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(const_cast<double *>(s.class_size), norm2.data(), C * sizeof(double),
+                             cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+    ENGINE_TRY(ld::engine_init(s, 0, ncols, c->stream, false));
+    ENGINE_TRY(ld::engine_modev(s, 0, 0, psig.as<double2>(), y.as<double>(), c->stream));
+    const int max_iter = c->opt.max_iter > 0 ? c->opt.max_iter : 100000;
+    int it = 0, remaining = 1, status = 0;
+    int64_t launches = 5;
+    while (it < max_iter && remaining > 0 && status == 0) {
+        for (int k = 0; k < 16 && it < max_iter; ++k, ++it) {
+            ENGINE_TRY(ld::engine_iteration(s, it & 1, c->stream));
+            ENGINE_TRY(ld::engine_modev(s, 1, (it & 1) ^ 1, psig.as<double2>(), y.as<double>(), c->stream));
+            launches += 3;
+        }
+        CUDA_TRY(cudaMemcpyAsync(c->h_pinned, s.remaining, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        remaining = c->h_pinned[0];
+        status = c->h_pinned[1];
+    }
+    CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+    std::vector<double> hy(elems);
+    CUDA_TRY(cudaMemcpyAsync(hy.data(), y.p, elems * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    float ms = 0.f;
+    CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    ld_status st = LD_OK;
+    if (status == ld::DEV_NOTSPD) st = fail(LD_ENOTSPD, "p^T Q p <= 0: Q is not SPD");
+    else if (status != 0) st = fail(LD_ENUMERIC, "non-finite CG scalar");
+    else if (remaining > 0) st = fail(LD_ENOTCONV, "max_iter reached");
+    fill_info(c, info, st, it, ms, launches, ms, 0);
+    if (st != LD_OK) return st;
+    for (int t = 0; t < nt; ++t)
+        for (int64_t i = 0; i < n; ++i)
+            for (int k = 0; k < T; ++k) {
+                const int col = t * T + k;
+                if (col < ncols) Y[i * ncols + col] = hy[((size_t)t * n + i) * T + k];
             }
     return LD_OK;
 }

@@ -348,9 +348,11 @@ __device__ void fused_tail(const Solve &s, int tile, int cur, const double *sums
     __syncthreads();
     for (int q = threadIdx.x; q < T * N; q += blockDim.x) {
         const int t = q / N, l = q - t * N, c = tile * T + t;
-        if (!sh_was[t]) continue;
         const int idx = c * N + l;
-        if (!s.sh_active[idx]) continue;
+        if (!sh_was[t] || !s.sh_active[idx]) {
+            if (s.asig) s.asig[idx] = make_double2(0.0, 0.0);   // no shifted-vector update
+            continue;
+        }
         const double alpha = sh_a[t], beta = sh_b[t];
         const double ap = s.alpha_prev[c], bp = s.beta_prev[c];
         const double2 sl = s.shift[l];
@@ -366,6 +368,10 @@ __device__ void fused_tail(const Solve &s, int tile, int cur, const double *sums
         const double2 bs = cscale(beta, cmul(ratio, ratio));
         const double2 phi = s.phi[idx];
         s.pi[idx] = cadd(s.pi[idx], cmul(as, phi));
+        if (s.asig) {   // shifted-vector mode: this iteration's coefficients
+            s.asig[idx] = as;
+            s.bsig[idx] = bs;
+        }
         s.phi[idx] = cadd(cscale(sh_vrn[t], zn), cmul(bs, phi));
         s.zeta_prev[idx] = z;
         s.zeta[idx] = zn;
@@ -1208,6 +1214,87 @@ struct BatchOcc {
     }
 };
 
+// ------------------------------------------------------------------ shifted vectors (mode V)
+// Optional vector form of CG-M: besides the projections, keep every shifted search
+// direction p^sigma (complex) and accumulate y = Re sum_l alpha_l x^{sigma_l} directly,
+//   x^sigma += alpha^sigma_k p^sigma_k,  p^sigma = zeta_{k+1} r_{k+1} + beta^sigma_k p^sigma,
+// with r_{k+1} = r_k - alpha_k w_k from the set the pass just wrote.  Gives log(Q) v for
+// arbitrary right-hand sides and cross-checks the projected recurrences.
+// psig: [ncols][N][n] complex; y: [ntiles][n][T] in FP64.
+template <typename V, int T>
+__global__ void k_modev(Solve s, int nxt, double2 *psig, double *y) {
+    const int64_t n = s.op.n;
+    const int N = s.nshift;
+    const int64_t total = (int64_t)s.ntiles * n;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int tile = (int)(q / n);
+        const int64_t i = q - (int64_t)tile * n;
+        const Pack<V, T> rk = ldpack<V, T, false>(static_cast<const V *>(nxt ? s.rbuf[1] : s.rbuf[0]), q);
+        const Pack<V, T> wk = ldpack<V, T, false>(static_cast<const V *>(nxt ? s.wbuf[1] : s.wbuf[0]), q);
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int c = tile * T + t;
+            const double r1 = (double)rk.v[t] - s.alpha[c] * (double)wk.v[t];   // r_{k+1}
+            double acc = 0.0;
+            for (int l = 0; l < N; ++l) {
+                const int idx = c * N + l;
+                const double2 as = s.asig[idx];
+                if (as.x == 0.0 && as.y == 0.0) continue;
+                double2 *pp = psig + (int64_t)idx * n + i;
+                const double2 p = *pp;
+                const double2 wgt = cmul(s.weight[l], as);          // alpha_l alpha^sigma
+                acc += wgt.x * p.x - wgt.y * p.y;                    // Re(alpha_l x^sigma increment)
+                const double2 zn = s.zeta[idx];
+                *pp = cadd(cscale(r1, zn), cmul(s.bsig[idx], p));
+            }
+            y[q * T + t] += acc;
+        }
+    }
+}
+
+__global__ void k_modev_clear(Solve s) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < s.ncols * s.nshift; q += gridDim.x * blockDim.x)
+        s.asig[q] = make_double2(0.0, 0.0);
+}
+
+// p^sigma_0 = v for every shift (v read from the initial residual set 0), y = 0
+template <typename V, int T>
+__global__ void k_modev_init(Solve s, double2 *psig, double *y) {
+    const int64_t n = s.op.n;
+    const int N = s.nshift;
+    const int64_t total = (int64_t)s.ntiles * n;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int tile = (int)(q / n);
+        const int64_t i = q - (int64_t)tile * n;
+        const Pack<V, T> r0 = ldpack<V, T, false>(static_cast<const V *>(s.rbuf[0]), q);
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int c = tile * T + t;
+            for (int l = 0; l < N; ++l) psig[((int64_t)c * N + l) * n + i] = make_double2((double)r0.v[t], 0.0);
+            y[q * T + t] = 0.0;
+        }
+    }
+}
+
+template <typename V, int T, int KIND>
+struct ModeVLauncher {
+    static int run(const Solve &s, int which, int nxt, double2 *psig, double *y, cudaStream_t st) {
+        const int64_t total = (int64_t)s.ntiles * s.op.n;
+        int blocks = (int)((total + 255) / 256);
+        if (blocks > 152 * 16) blocks = 152 * 16;
+        if (blocks < 1) blocks = 1;
+        if (which == 0)
+            k_modev_init<V, T><<<blocks, 256, 0, st>>>(s, psig, y);
+        else {
+            k_modev<V, T><<<blocks, 256, 0, st>>>(s, nxt, psig, y);
+            k_modev_clear<<<64, 256, 0, st>>>(s);
+        }
+        return (int)cudaGetLastError();
+    }
+};
+
 // ------------------------------------------------------------------ init / flush / finish
 template <typename V, int T>
 __global__ void k_init_vectors(Solve s) {
@@ -1586,7 +1673,7 @@ int engine_plan(Solve &s) {
     return s.bpt;
 }
 
-int engine_init(const Solve &s, int col_begin, int col_end, void *stream) {
+int engine_init(const Solve &s, int col_begin, int col_end, void *stream, bool vectors) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     k_init_scalars<<<64, 256, 0, st>>>(s, col_begin, col_end, s.class_size);
     int e = (int)cudaGetLastError();
@@ -1594,6 +1681,7 @@ int engine_init(const Solve &s, int col_begin, int col_end, void *stream) {
     k_init_tiles<<<1, 256, 0, st>>>(s);
     e = (int)cudaGetLastError();
     if (e) return e;
+    if (!vectors) return 0;
     return dispatch<InitLauncher>(s.precision, s.T, s.op.kind, s, st);
 }
 
@@ -1627,6 +1715,11 @@ int engine_batch(const Solve *solves_dev, const int *ncolours_dev, int count, co
     k_batch_finish<<<(count + 127) / 128, 128, 0, st>>>(solves_dev, ncolours_dev, count, logdet_dev,
                                                        seed_dev, flag_dev, iters_dev);
     return (int)cudaGetLastError();
+}
+
+int engine_modev(const Solve &s, int which, int nxt, double2 *psig, double *y, void *stream) {
+    return dispatch<ModeVLauncher>(s.precision, s.T, s.op.kind, s, which, nxt, psig, y,
+                                   static_cast<cudaStream_t>(stream));
 }
 
 int engine_flush_x(const Solve &s, void *stream) {

@@ -71,6 +71,7 @@ struct Solve {
     // per (column, shift): [ncols][nshift]
     double2 *zeta, *zeta_prev, *pi, *phi;
     uint8_t *sh_active;
+    double2 *asig, *bsig;  // shifted-vector mode: alpha^sigma, beta^sigma of the last pass (or null)
     const double2 *shift;  // s_l = -sigma_l
     const double2 *weight; // alpha_l
     // per tile
@@ -87,10 +88,13 @@ struct Solve {
 constexpr int NDOT = 6;
 
 // Engine entry points (engine.cu); all asynchronous on `stream`.
-int engine_init(const Solve &s, int col_begin, int col_end, void *stream);
+int engine_init(const Solve &s, int col_begin, int col_end, void *stream, bool vectors = true);
 int engine_iteration(const Solve &s, int parity, void *stream);      // one fused CG pass
 int engine_cta_solve(const Solve &s, int max_iter, void *stream);    // whole solve, one CTA per tile
 int engine_flush_x(const Solve &s, void *stream);                    // last seed-solution update
+// shifted-vector mode: which = 0 init (p^sigma = v, y = 0), 1 update after a pass that
+// wrote set `nxt`
+int engine_modev(const Solve &s, int which, int nxt, double2 *psig, double *y, void *stream);
 // batched engine: all instances' tiles in one persistent launch (plus prep/finish)
 int engine_batch_occupancy(int precision, int T);
 int engine_batch(const Solve *solves_dev, const int *ncolours_dev, int count, const int2 *items_dev,
