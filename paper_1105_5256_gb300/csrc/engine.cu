@@ -992,6 +992,168 @@ __global__ void __launch_bounds__(SW * G, stream_min_blocks_t<V, T>()) k_stream2
     publish_and_tail<K>(s, tile, cur, cta, reinterpret_cast<double *>(smem));
 }
 
+// ------------------------------------------------------------------ streaming 3D engine
+// The 7-point kind streams along z: a CTA owns a P3X x P3Y tile of lattice columns
+// (a 1-wide halo all around, (P3X-2) x (P3Y-2) of its own) and a segment of
+// planes, one thread per lattice column holding all T probing columns.  Per plane
+// step: (r, w, p) of plane z arrive from the per-thread cp.async ring, p_k(z) goes
+// to a double-buffered shared plane, and w = Q p_k at plane z-1 takes its in-plane
+// neighbours from the shared plane written last step and its z neighbours from the
+// thread's register window.  Out-of-grid entries are zero (Dirichlet ghosts of the
+// difference form); a torus wraps.
+constexpr int P3X = 32, P3Y = 8, P3T = P3X * P3Y;
+
+template <typename V, int T>
+constexpr size_t stream3d_smem_bytes() {
+    constexpr size_t pk = sizeof(Pack<V, T>);
+    constexpr size_t rows = (2 + 3 * STREAM_PD) * P3T * pk + STREAM_PD * P3T * sizeof(int);
+    constexpr size_t part = (size_t)P3T * NDOT * T * sizeof(V);
+    constexpr size_t red = (size_t)P3T * sizeof(double);
+    return rows > part ? (rows > red ? rows : red) : (part > red ? part : red);
+}
+
+template <typename V, int T>
+__host__ __device__ constexpr int stream3d_min_blocks() { return sizeof(V) * T <= 8 ? 3 : 2; }
+
+template <typename V, int T, bool KEEPX>
+__global__ void __launch_bounds__(P3T, stream3d_min_blocks<V, T>()) k_stream3d(Solve s, int cur) {
+    constexpr int K = NDOT * T, PD = STREAM_PD, H = 1;
+    using P = Pack<V, T>;
+    using M = PackMath<V, T>;
+    const int tile = blockIdx.y;
+    if (s.tile_done[tile]) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    P *const ps = reinterpret_cast<P *>(smem);                    // 2 planes
+    P *const ring = ps + 2 * P3T + threadIdx.x;
+    int *const ringc = reinterpret_cast<int *>(ps + (2 + 3 * PD) * P3T) + threadIdx.x;
+    const int nx = s.op.nx, ny = s.op.ny, nz = s.op.nz;
+    const bool per = s.op.periodic;
+    const int xl = threadIdx.x % P3X, yl = threadIdx.x / P3X;
+    const int tx = (nx + P3X - 3) / (P3X - 2);                    // x tiles
+    const int xy = blockIdx.x % s.strips, sg = blockIdx.x / s.strips;
+    const int bx = xy % tx, by = xy / tx;
+    const int gx = bx * (P3X - 2) - 1 + xl, gy = by * (P3Y - 2) - 1 + yl;
+    bool inx, iny;
+    const int gxw = wrap_coord(gx, nx, per, inx);
+    const int gyw = wrap_coord(gy, ny, per, iny);
+    const bool inxy = inx && iny;
+    const bool out = xl >= 1 && xl < P3X - 1 && yl >= 1 && yl < P3Y - 1 && gx < nx && gy < ny;
+    const int zs = sg * s.seg, ze = min(zs + s.seg, nz);
+    const int cb = tile * T;
+    const int64_t off = (int64_t)tile * s.op.n * T;
+    const int64_t plane = (int64_t)nx * ny;
+    const V *const r = static_cast<const V *>(cur ? s.rbuf[1] : s.rbuf[0]) + off;
+    const V *const w = static_cast<const V *>(cur ? s.wbuf[1] : s.wbuf[0]) + off;
+    const V *const p = static_cast<const V *>(cur ? s.pbuf[1] : s.pbuf[0]) + off;
+    P na, b;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        na.v[t] = -(V)s.alpha[cb + t];
+        b.v[t] = (V)s.beta[cb + t];
+    }
+    StreamAcc<V, T> acc;
+    acc.zero();
+    int z = zs - H;
+    const int zend = ze + H;
+    const int64_t col_off = (int64_t)gyw * nx + gxw;
+    auto load_plane = [&](int zr, int slot) {
+        bool inz;
+        const int gzw = wrap_coord(zr, nz, per, inz);
+        const bool in = inz && inxy && zr < zend;
+        const int64_t vtx = in ? (int64_t)gzw * plane + col_off : 0;
+        const int64_t e = vtx * T;
+        P *q = ring + slot * 3 * P3T;
+        cp_async_pack<V, T>(q, r + e, in);
+        cp_async_pack<V, T>(q + P3T, w + e, in);
+        cp_async_pack<V, T>(q + 2 * P3T, p + e, in);
+        const unsigned dc = (unsigned)__cvta_generic_to_shared(ringc + slot * P3T);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dc),
+                     "l"(s.colour + vtx), "r"(in ? 4 : 0));
+        cp_async_commit();
+    };
+    P pw0 = zero_pack<V, T>(), pw1 = pw0, pw2 = pw0;   // p at planes z-2, z-1, z
+    const P sc = M::splat((V)s.op.scale);
+    // ring slot of plane zr is (zr - z0) mod PD (see the 2D sweep for the schedule)
+#pragma unroll
+    for (int k = 0; k < PD - H; ++k) load_plane(z + k, k);
+    int slot = 0;
+    for (; z < zend; ++z) {
+        cp_async_wait<PD - 1 - H>();
+        {
+            const P *q = ring + slot * 3 * P3T;
+            const P pk = M::fma(b, q[2 * P3T], M::fma(na, q[P3T], q[0]));
+            ps[(z & 1) * P3T + threadIdx.x] = pk;
+            pw0 = pw1;
+            pw1 = pw2;
+            pw2 = pk;
+        }
+        const int slot_h = slot - H < 0 ? slot - H + PD : slot - H;
+        if (z - 1 >= zs && z - 1 < ze && out) {
+            const int64_t gi = (int64_t)(z - 1) * plane + (int64_t)gy * nx + gx;
+            V dg = field_at<V>(s.op, gi);
+            if (s.op.mask) dg += (V)s.op.tau * (V)s.op.mask[gi];
+            const P *pl = ps + ((z - 1) & 1) * P3T;
+            const P c = pw1;
+            const P h = M::add(M::add(M::sub(c, pl[threadIdx.x - 1]), M::sub(c, pl[threadIdx.x + 1])),
+                               M::add(M::sub(c, pl[threadIdx.x - P3X]), M::sub(c, pl[threadIdx.x + P3X])));
+            const P v = M::add(M::sub(c, pw0), M::sub(c, pw2));
+            const P wk = M::mul(sc, M::fma(M::splat(dg), c, M::add(h, v)));
+            // outputs at (gx, gy, z-1)
+            const P *q = ring + slot_h * 3 * P3T;
+            const P rk = M::fma(na, q[P3T], q[0]);
+            const int64_t e = gi * T;
+            *reinterpret_cast<P *>(static_cast<V *>(cur ? s.rbuf[0] : s.rbuf[1]) + off + e) = rk;
+            *reinterpret_cast<P *>(static_cast<V *>(cur ? s.pbuf[0] : s.pbuf[1]) + off + e) = c;
+            *reinterpret_cast<P *>(static_cast<V *>(cur ? s.wbuf[0] : s.wbuf[1]) + off + e) = wk;
+            if constexpr (KEEPX) {
+                V *x = static_cast<V *>(s.x) + off;
+                const P xo = *reinterpret_cast<const P *>(x + e);
+                *reinterpret_cast<P *>(x + e) = M::fma(M::neg(na), q[2 * P3T], xo);
+            }
+            const int lc = ringc[slot_h * P3T] - cb;
+            acc.rr = M::fma(rk, rk, acc.rr);
+            acc.pw = M::fma(c, wk, acc.pw);
+            acc.rw = M::fma(rk, wk, acc.rw);
+            acc.ww = M::fma(wk, wk, acc.ww);
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                if (lc == t) {
+                    acc.vr[t] += rk.v[t];
+                    acc.vw[t] += wk.v[t];
+                }
+            }
+        }
+        load_plane(z - H + PD, slot_h);
+        slot = slot + 1 == PD ? 0 : slot + 1;
+        __syncthreads();
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+    // CTA sums: per-thread partials -> shared, one thread per (dot, column) adds them
+    V *part = reinterpret_cast<V *>(smem);
+    {
+        V *mine = part + threadIdx.x * NDOT * T;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            mine[0 * T + t] = acc.rr.v[t];
+            mine[1 * T + t] = acc.pw.v[t];
+            mine[2 * T + t] = acc.rw.v[t];
+            mine[3 * T + t] = acc.ww.v[t];
+            mine[4 * T + t] = acc.vr[t];
+            mine[5 * T + t] = acc.vw[t];
+        }
+    }
+    __syncthreads();
+    __shared__ double cta[K];
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        double a = 0.0;
+        for (int th = 0; th < P3T; ++th) a += (double)part[th * NDOT * T + k];
+        cta[k] = a;
+    }
+    __syncthreads();
+    publish_and_tail<K>(s, tile, cur, cta, reinterpret_cast<double *>(smem));
+}
+
 // ------------------------------------------------------------------ CTA engine
 // One CTA runs a tile's whole solve (small problems): the same fused pass,
 // block barriers only, sets alternating inside the kernel (coherent loads).
@@ -1571,6 +1733,11 @@ struct IterLauncher {
                 k_stream2d<V, T, G, KIND, true><<<grid, SW * G, stream_smem_bytes<V, T, G>(), st>>>(s, cur);
             else
                 k_stream2d<V, T, G, KIND, false><<<grid, SW * G, stream_smem_bytes<V, T, G>(), st>>>(s, cur);
+        } else if constexpr (KIND == KIND_3D7) {
+            if (s.keep_x0)
+                k_stream3d<V, T, true><<<grid, P3T, stream3d_smem_bytes<V, T>(), st>>>(s, cur);
+            else
+                k_stream3d<V, T, false><<<grid, P3T, stream3d_smem_bytes<V, T>(), st>>>(s, cur);
         } else {
             k_pass<V, T, KIND><<<grid, 256, 0, st>>>(s, cur);
         }
@@ -1637,6 +1804,14 @@ struct OccLauncher {
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
                 return (int)cudaGetLastError();
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_stream2d<V, T, G, KIND, true>, SW * G, sm);
+        } else if constexpr (KIND == KIND_3D7) {
+            constexpr size_t sm = stream3d_smem_bytes<V, T>();
+            if (cudaFuncSetAttribute(k_stream3d<V, T, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+                cudaFuncSetAttribute(k_stream3d<V, T, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+                return (int)cudaGetLastError();
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_stream3d<V, T, true>, P3T, sm);
         } else {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pass<V, T, KIND>, 256, 0);
         }
@@ -1662,6 +1837,18 @@ int engine_plan(Solve &s) {
         if (nsegs > s.op.ny) nsegs = s.op.ny;
         s.seg = (int)((s.op.ny + nsegs - 1) / nsegs);
         nsegs = (s.op.ny + s.seg - 1) / s.seg;
+        s.bpt = (int)(s.strips * nsegs);
+        return s.bpt;
+    }
+    if (s.op.kind == KIND_3D7) {
+        // one CTA per (x-y tile, z segment); segments only when the x-y tiles are too few
+        const int tx = (s.op.nx + P3X - 3) / (P3X - 2), ty = (s.op.ny + P3Y - 3) / (P3Y - 2);
+        s.strips = tx * ty;
+        int64_t nsegs = target / ((int64_t)s.strips * s.ntiles);
+        if (nsegs < 1) nsegs = 1;
+        if (nsegs > s.op.nz) nsegs = s.op.nz;
+        s.seg = (int)((s.op.nz + nsegs - 1) / nsegs);
+        nsegs = (s.op.nz + s.seg - 1) / s.seg;
         s.bpt = (int)(s.strips * nsegs);
         return s.bpt;
     }
