@@ -135,16 +135,24 @@ def algorithmic_bytes(n, T, prec, tile_iters, passes):
     return 6 * n * T * w * tile_iters + 4 * n * passes
 
 
+def pass_kernel_sha256():
+    """sha256 over the sources of the pass kernels (device code and their launcher)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("engine_device.cuh", "engine_iter.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1105_5256_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()
+
+
 def recorded_traffic(tile_width):
     """DRAM bytes per full launch of the pass kernel from the committed ncu summary, or
     None when the engine source changed since that capture (or no summary matches)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "k_stream2d_matern1024_T%d.md" % tile_width)
-    src = os.path.join(ROOT, "paper_1105_5256_gb300", "csrc", "engine.cu")
     try:
         rec = dict(line.split(": ", 1) for line in open(path).read().splitlines()
                    if line.startswith(("engine_sha256: ", "traffic_bytes_per_launch: ")))
-        cur = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        cur = pass_kernel_sha256()
         if rec.get("engine_sha256", "").strip() != cur:
             return None
         return float(rec["traffic_bytes_per_launch"])

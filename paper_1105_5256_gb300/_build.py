@@ -17,8 +17,9 @@ OUT = os.path.join(PKG, "liblogdet.so")
 BUILD = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["engine.cu", "static_scratch.cu"]
+CU_SOURCES = ["engine.cu", "engine_iter_f32.cu", "engine_iter_f64.cu", "static_scratch.cu"]
 CXX_SOURCES = ["api.cpp", "colouring.cpp", "hht.cpp"]
+HEADERS = ["internal.h", "engine_device.cuh", "engine_iter.cuh"]
 
 
 def _cuda_home() -> str:
@@ -29,8 +30,8 @@ def _cuda_home() -> str:
 
 
 def _sources():
-    return [os.path.join(CSRC, s) for s in CU_SOURCES + CXX_SOURCES] + [
-        os.path.join(CSRC, "internal.h"), os.path.join(ROOT, "include", "logdet.h")]
+    return [os.path.join(CSRC, s) for s in CU_SOURCES + CXX_SOURCES + HEADERS] + [
+        os.path.join(ROOT, "include", "logdet.h")]
 
 
 def _stale() -> bool:

@@ -1,0 +1,71 @@
+// Launch and occupancy of the per-iteration pass kernels, instantiated per
+// precision by engine_iter_f32.cu and engine_iter_f64.cu.
+#pragma once
+#include "engine_device.cuh"
+
+namespace ld {
+
+template <typename V, int T, int KIND>
+struct IterLauncher {
+    static int run(const Solve &s, int cur, cudaStream_t st) {
+        dim3 grid(s.bpt, s.ntiles);
+        if constexpr (KIND == KIND_2D5 || KIND == KIND_2D13_SQ) {
+            constexpr int G = stream_groups<V, T>();
+            if (s.keep_x0)
+                k_stream2d<V, T, G, KIND, true><<<grid, SW * G, stream_smem_bytes<V, T, G>(), st>>>(s, cur);
+            else
+                k_stream2d<V, T, G, KIND, false><<<grid, SW * G, stream_smem_bytes<V, T, G>(), st>>>(s, cur);
+        } else if constexpr (KIND == KIND_3D7) {
+            if (s.keep_x0)
+                k_stream3d<V, T, true><<<grid, P3T, stream3d_smem_bytes<V, T>(), st>>>(s, cur);
+            else
+                k_stream3d<V, T, false><<<grid, P3T, stream3d_smem_bytes<V, T>(), st>>>(s, cur);
+        } else {
+            k_pass<V, T, KIND><<<grid, 256, 0, st>>>(s, cur);
+        }
+        return (int)cudaGetLastError();
+    }
+};
+
+template <typename V, int T, int KIND>
+struct OccLauncher {
+    // resident CTAs per SM of the iteration kernels (the smaller of the two phases)
+    static int run(int *out) {
+        int a = 0, b = 0;
+        if constexpr (KIND == KIND_2D5 || KIND == KIND_2D13_SQ) {
+            constexpr int G = stream_groups<V, T>();
+            constexpr size_t sm = stream_smem_bytes<V, T, G>();
+            if (cudaFuncSetAttribute(k_stream2d<V, T, G, KIND, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+                cudaFuncSetAttribute(k_stream2d<V, T, G, KIND, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+                return (int)cudaGetLastError();
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_stream2d<V, T, G, KIND, true>, SW * G, sm);
+        } else if constexpr (KIND == KIND_3D7) {
+            constexpr size_t sm = stream3d_smem_bytes<V, T>();
+            if (cudaFuncSetAttribute(k_stream3d<V, T, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+                cudaFuncSetAttribute(k_stream3d<V, T, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+                return (int)cudaGetLastError();
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_stream3d<V, T, true>, P3T, sm);
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pass<V, T, KIND>, 256, 0);
+        }
+        (void)b;
+        *out = a;
+        return (int)cudaGetLastError();
+    }
+};
+
+template <typename V>
+int iteration_launch(const Solve &s, int cur, cudaStream_t st) {
+    return dispatch_v<V, IterLauncher>(s.T, s.op.kind, s, cur, st);
+}
+
+template <typename V>
+int iteration_occupancy(int T, int kind, int *occ) {
+    return dispatch_v<V, OccLauncher>(T, kind, occ);
+}
+
+}  // namespace ld
