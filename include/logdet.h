@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define LD_ABI_VERSION 1
+#define LD_ABI_VERSION 2
 
 typedef struct ld_ctx ld_ctx;
 
@@ -113,6 +113,8 @@ typedef struct {
                                  iteration launch on the context stream) */
     int64_t tile_iters;       /* sum over tiles of the iterations each tile ran */
     int64_t gpu_launches;     /* kernels this call launched (graph nodes counted) */
+    int32_t bulk_rows;        /* grid engine on a 2D lattice: 1 when lattice rows move by
+                                 bulk (TMA) copies, 0 by per-thread copies; -1 otherwise */
 } ld_info;
 
 /* ABI version (LD_ABI_VERSION).  Never fails. */

@@ -57,7 +57,7 @@ class Info(C.Structure):
                 ("iters", C.c_int32), ("tile_width", C.c_int32), ("engine", C.c_int32),
                 ("lambda_min", C.c_double), ("lambda_max", C.c_double), ("quad_cert", C.c_double),
                 ("ms", C.c_double), ("iter_ms", C.c_double), ("tile_iters", C.c_int64),
-                ("gpu_launches", C.c_int64)]
+                ("gpu_launches", C.c_int64), ("bulk_rows", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

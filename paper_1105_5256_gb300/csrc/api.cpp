@@ -113,6 +113,11 @@ struct ld_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_chunk = 0;
+    // grid engine: tile groups iterate on their own streams inside the captured graph
+    static constexpr int kMaxGroups = 16;
+    int ngroups = 0;
+    cudaStream_t gstream[kMaxGroups] = {};
+    cudaEvent_t gfork = nullptr, gjoin[kMaxGroups] = {};
     int32_t *h_pinned = nullptr;  // remaining, status
     bool have_x0 = false;
     int last_cb = 0, last_ce = 0;
@@ -133,6 +138,11 @@ struct ld_ctx {
         if (ev2) cudaEventDestroy(ev2);
         if (ev3) cudaEventDestroy(ev3);
         if (h_pinned) cudaFreeHost(h_pinned);
+        for (int g = 0; g < kMaxGroups; ++g) {
+            if (gstream[g]) cudaStreamDestroy(gstream[g]);
+            if (gjoin[g]) cudaEventDestroy(gjoin[g]);
+        }
+        if (gfork) cudaEventDestroy(gfork);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 };
@@ -279,6 +289,7 @@ void fill_operator(ld_ctx *c) {
     op.kappa2 = c->kappa2;
     op.tau = c->tau;
     op.scale = c->kind == LD_CSR ? 1.0 : c->scale;
+    ld::set_f32_coefs(op);
     op.field_d = c->d_field_d.as<double>();
     op.field_f = c->d_field_f.as<float>();
     op.mask = c->d_mask.as<uint8_t>();
@@ -293,13 +304,43 @@ void invalidate_graph(ld_ctx *c) {
     c->graph = nullptr;
 }
 
+// Tile groups of the grid engine: tiles are independent solves, so each group
+// (tiles g, g + G, ...) iterates on its own stream and one group's end-of-pass
+// reduction and last CTAs overlap the other groups' sweeps.
+ld_status ensure_groups(ld_ctx *c) {
+    const int want = std::min(c->ntiles, (int)ld_ctx::kMaxGroups);
+    if (c->ngroups == want) return LD_OK;
+    if (!c->gfork) CUDA_TRY(cudaEventCreateWithFlags(&c->gfork, cudaEventDisableTiming));
+    for (int g = 0; g < want; ++g) {
+        if (!c->gstream[g]) CUDA_TRY(cudaStreamCreateWithFlags(&c->gstream[g], cudaStreamNonBlocking));
+        if (!c->gjoin[g]) CUDA_TRY(cudaEventCreateWithFlags(&c->gjoin[g], cudaEventDisableTiming));
+    }
+    c->ngroups = want;
+    return LD_OK;
+}
+
 ld_status ensure_graph(ld_ctx *c) {
     if (c->graph && c->graph_chunk == c->chunk) return LD_OK;
     invalidate_graph(c);
+    if (ld_status st = ensure_groups(c)) return st;
     cudaGraph_t g = nullptr;
     CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     int err = 0;
-    for (int j = 0; j < c->chunk && !err; ++j) err = ld::engine_iteration(c->s, j & 1, c->stream);
+    const int G = c->ngroups;
+    if (G <= 1) {
+        for (int j = 0; j < c->chunk && !err; ++j) err = ld::engine_iteration(c->s, j & 1, c->stream);
+    } else {
+        err = (int)cudaEventRecord(c->gfork, c->stream);
+        for (int gi = 0; gi < G && !err; ++gi) {
+            err = (int)cudaStreamWaitEvent(c->gstream[gi], c->gfork, 0);
+            Solve sg = c->s;
+            sg.tile0 = gi;
+            sg.tstride = G;
+            for (int j = 0; j < c->chunk && !err; ++j) err = ld::engine_iteration(sg, j & 1, c->gstream[gi]);
+            if (!err) err = (int)cudaEventRecord(c->gjoin[gi], c->gstream[gi]);
+            if (!err) err = (int)cudaStreamWaitEvent(c->stream, c->gjoin[gi], 0);
+        }
+    }
     cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
     if (err) {
         if (g) cudaGraphDestroy(g);
@@ -332,6 +373,8 @@ void fill_info(const ld_ctx *c, ld_info *info, ld_status st, int iters, float ms
     info->quad_cert = c->cert;
     info->ms = ms;
     info->gpu_launches = launches;
+    const bool lattice2d = c->s.op.kind == ld::KIND_2D5 || c->s.op.kind == ld::KIND_2D13_SQ;
+    info->bulk_rows = c->engine == 1 && lattice2d ? c->s.bulk : -1;
 }
 
 // One probed solve over colours [cb, ce).  On LD_OK, result[0..1] hold
@@ -377,7 +420,7 @@ ld_status run_solve(ld_ctx *c, int cb, int ce, bool keep_x0, double out[2], ld_i
             CUDA_TRY(cudaEventRecord(c->ev2, c->stream));
             CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
             CUDA_TRY(cudaEventRecord(c->ev3, c->stream));
-            launches += c->chunk;
+            launches += (int64_t)c->chunk * std::max(c->ngroups, 1);
             done_iters += c->chunk;
             CUDA_TRY(cudaMemcpyAsync(c->h_pinned, c->s.remaining, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
             CUDA_TRY(cudaMemcpyAsync(c->h_pinned + 1, c->s.status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
@@ -1193,6 +1236,7 @@ ld_status ld_batch_logdet(ld_ctx *c, double *logdets, double *grads, ld_info *in
         info->ms = ms;
         info->iter_ms = ms;
         info->gpu_launches = 3;
+        info->bulk_rows = -1;
         int64_t ti = 0;
         for (int i = 0; i < count; ++i) ti += (int64_t)c->subs[i]->ntiles * flags[count + i];
         info->tile_iters = ti;   // upper bound: every tile counted at its instance's iterations

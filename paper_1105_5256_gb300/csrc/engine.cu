@@ -591,8 +591,13 @@ int engine_plan(Solve &s) {
     int dev = 0, sms = 152, occ = 8;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int oe = s.precision == 0 ? iteration_occupancy<double>(s.T, s.op.kind, &occ)
-                                    : iteration_occupancy<float>(s.T, s.op.kind, &occ);
+    const bool lattice2d = s.op.kind == KIND_2D5 || s.op.kind == KIND_2D13_SQ;
+    // bulk row copies measured faster for packs of 24 bytes and more; per-thread
+    // copies win for 8- and 16-byte packs (fewer instructions on the critical path)
+    const int pack_bytes = s.T * (s.precision == 0 ? (int)sizeof(double) : (int)sizeof(float));
+    s.bulk = lattice2d && pack_bytes >= 24 && stream_bulk_ok(s.op.nx, pack_bytes);
+    const int oe = s.precision == 0 ? iteration_occupancy<double>(s.T, s.op.kind, s.bulk != 0, &occ)
+                                    : iteration_occupancy<float>(s.T, s.op.kind, s.bulk != 0, &occ);
     if (oe != 0 || occ < 1) occ = 1;
     const int64_t target = (int64_t)sms * occ;   // exactly one resident wave
     s.strips = 1;

@@ -108,6 +108,23 @@ __device__ __forceinline__ void axpy(V (&w)[T], V c, const V (&a)[T]) {
     for (int t = 0; t < T; ++t) w[t] = fma(c, a[t], w[t]);
 }
 
+// operator coefficients in the vector precision (no conversion in FP32 kernels)
+template <typename V>
+__device__ __forceinline__ V op_kappa2(const Operator &op) {
+    if constexpr (sizeof(V) == 8) return op.kappa2;
+    else return op.kappa2_f;
+}
+template <typename V>
+__device__ __forceinline__ V op_tau(const Operator &op) {
+    if constexpr (sizeof(V) == 8) return op.tau;
+    else return op.tau_f;
+}
+template <typename V>
+__device__ __forceinline__ V op_scale(const Operator &op) {
+    if constexpr (sizeof(V) == 8) return op.scale;
+    else return op.scale_f;
+}
+
 template <typename V>
 __device__ __forceinline__ V field_at(const Operator &op, int64_t i);
 template <>
@@ -116,7 +133,7 @@ __device__ __forceinline__ double field_at<double>(const Operator &op, int64_t i
 }
 template <>
 __device__ __forceinline__ float field_at<float>(const Operator &op, int64_t i) {
-    return op.field_f ? (float)op.kappa2 * op.field_f[i] : (float)op.kappa2;
+    return op.field_f ? op.kappa2_f * op.field_f[i] : op.kappa2_f;
 }
 
 // Lattice neighbour of (x, y, z) shifted by (dx, dy, dz): wrapped on a torus,
@@ -182,8 +199,8 @@ __device__ __forceinline__ void apply_row(const Operator &op, int64_t i, const L
             }
         }
         V dg = field_at<V>(op, i) + (V)(NB - nb);
-        if (op.mask) dg += (V)op.tau * (V)op.mask[i];
-        const V sc = (V)op.scale;
+        if (op.mask) dg += op_tau<V>(op) * (V)op.mask[i];
+        const V sc = op_scale<V>(op);
 #pragma unroll
         for (int t = 0; t < T; ++t) w[t] = sc * fma(dg, self[t], acc[t]);
     } else if constexpr (KIND == KIND_2D13_SQ) {
@@ -192,7 +209,7 @@ __device__ __forceinline__ void apply_row(const Operator &op, int64_t i, const L
         const int nx = op.nx;
         const int y = (int)(i / nx);
         const int x = (int)(i - (int64_t)y * nx);
-        const V k2 = (V)op.kappa2;
+        const V k2 = op_kappa2<V>(op);
         const int DX[4] = {-1, 1, 0, 0}, DY[4] = {0, 0, -1, 1};
         V uc[T];
 #pragma unroll
@@ -242,7 +259,7 @@ __device__ __forceinline__ void apply_row(const Operator &op, int64_t i, const L
 #pragma unroll
         for (int q = 0; q < 4; ++q)
             if (has[q]) diff_accum(acc, uc, u[q]);
-        const V sc = (V)op.scale;
+        const V sc = op_scale<V>(op);
 #pragma unroll
         for (int t = 0; t < T; ++t) w[t] = sc * fma(dc, uc[t], acc[t]);
     } else {  // CSR (values pre-scaled)
@@ -263,23 +280,17 @@ __device__ __forceinline__ void apply_row(const Operator &op, int64_t i, const L
 // ------------------------------------------------------------------ reductions
 __device__ __forceinline__ void set_status(int32_t *st, int code) { atomicCAS(st, 0, code); }
 
+// tile of this CTA in a grid-engine pass launch (grid.y = tiles of the launch)
+__device__ __forceinline__ int launch_tile(const Solve &s) {
+    return s.tile0 + (int)blockIdx.y * (s.tstride > 0 ? s.tstride : 1);
+}
+
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
-    // Smith's algorithm
-    if (fabs(b.x) >= fabs(b.y)) {
-        double r = b.y / b.x, d = b.x + b.y * r;
-        return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
-    } else {
-        double r = b.x / b.y, d = b.y + b.x * r;
-        return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
-    }
 }
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 cscale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
-__device__ __forceinline__ double cabs2(double2 a) { return hypot(a.x, a.y); }
 
 // ------------------------------------------------------------------ fused CG-M pass
 // One pass per CG iteration k, for every column of a tile (Sec. 2.1: the real
@@ -316,7 +327,7 @@ struct LoadFused {
 // sums[k*T + t] = dot k of column t (order: rr, pw, rw, ww, vr, vw).
 static __device__ void fused_tail(const Solve &s, int tile, int cur, const double *sums) {
     const int T = s.T, N = s.nshift;
-    __shared__ double sh_a[32], sh_b[32], sh_vrn[32], sh_rhon[32];
+    __shared__ double sh_a[32], sh_b[32], sh_vrn[32], sh_res[32], sh_lim[32];
     __shared__ int sh_was[32], sh_any[32];
     if (threadIdx.x < T) {
         const int t = threadIdx.x, c = tile * T + t;
@@ -324,6 +335,7 @@ static __device__ void fused_tail(const Solve &s, int tile, int cur, const doubl
         sh_was[t] = act;
         sh_any[t] = 0;
         double a = 0.0, b = 0.0, vrn = 0.0, rhon = 0.0;
+        const double lim = s.tol * sqrt(s.vnorm2[c]);
         if (act) {
             const double rr = sums[0 * T + t], pw = sums[1 * T + t], rw = sums[2 * T + t];
             const double ww = sums[3 * T + t], vr = sums[4 * T + t], vw = sums[5 * T + t];
@@ -340,15 +352,19 @@ static __device__ void fused_tail(const Solve &s, int tile, int cur, const doubl
             s.pi0[c] += a * s.phi0[c];
             s.phi0[c] = vrn + b * s.phi0[c];
             s.rho[c] = rhon;
-            if (sqrt(rhon) > s.tol * sqrt(s.vnorm2[c])) sh_any[t] = 1;
+            if (sqrt(rhon) > lim) sh_any[t] = 1;
         }
         sh_a[t] = a;
         sh_b[t] = b;
         sh_vrn[t] = vrn;
-        sh_rhon[t] = rhon;
+        sh_res[t] = sqrt(rhon);     // ||r_{k+1}||: shifted residual = |zeta_{k+1}| ||r_{k+1}||
+        sh_lim[t] = lim;
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < T * N; q += blockDim.x) {
+    // one (column, shift) item per thread, spread over the warps (FP64 work on every
+    // scheduler): item q = lane * warps + warp
+    const int nw = blockDim.x >> 5;
+    for (int q = (threadIdx.x & 31) * nw + (threadIdx.x >> 5); q < T * N; q += blockDim.x) {
         const int t = q / N, l = q - t * N, c = tile * T + t;
         const int idx = c * N + l;
         if (!sh_was[t] || !s.sh_active[idx]) {
@@ -360,12 +376,13 @@ static __device__ void fused_tail(const Solve &s, int tile, int cur, const doubl
         const double2 sl = s.shift[l];
         const double2 z = s.zeta[idx], zp = s.zeta_prev[idx];
         // zeta_{k+1} = zeta_k zeta_{k-1} a_{k-1} /
-        //              (a_{k-1} zeta_{k-1} (1 + s a_k) + a_k b_{k-1} (zeta_{k-1} - zeta_k))
-        const double2 num = cscale(ap, cmul(z, zp));
+        //              (a_{k-1} zeta_{k-1} (1 + s a_k) + a_k b_{k-1} (zeta_{k-1} - zeta_k)),
+        // formed as ratio = zeta_{k+1} / zeta_k = a_{k-1} zeta_{k-1} / den (one division)
         const double2 one_sa = make_double2(1.0 + sl.x * alpha, sl.y * alpha);
         const double2 den = cadd(cscale(ap, cmul(zp, one_sa)), cscale(alpha * bp, csub(zp, z)));
-        const double2 zn = cdiv(num, den);
-        const double2 ratio = cdiv(zn, z);
+        const double inv = 1.0 / (den.x * den.x + den.y * den.y);
+        const double2 ratio = cscale(ap * inv, cmul(zp, make_double2(den.x, -den.y)));
+        const double2 zn = cmul(ratio, z);
         const double2 as = cscale(alpha, ratio);
         const double2 bs = cscale(beta, cmul(ratio, ratio));
         const double2 phi = s.phi[idx];
@@ -377,9 +394,9 @@ static __device__ void fused_tail(const Solve &s, int tile, int cur, const doubl
         s.phi[idx] = cadd(cscale(sh_vrn[t], zn), cmul(bs, phi));
         s.zeta_prev[idx] = z;
         s.zeta[idx] = zn;
-        const double res = cabs2(zn) * sqrt(sh_rhon[t]);
+        const double res = sqrt(zn.x * zn.x + zn.y * zn.y) * sh_res[t];
         if (!isfinite(res)) set_status(s.status, DEV_NUMERIC);
-        if (res > s.tol * sqrt(s.vnorm2[c])) {
+        if (res > sh_lim[t]) {
             atomicOr(&sh_any[t], 1);
         } else {
             s.sh_active[idx] = 0;
@@ -521,12 +538,14 @@ __device__ __forceinline__ bool tile_last_block(const Solve &s, int tile) {
 template <typename A, int K>
 __device__ __forceinline__ void block_sum_to(const A (&v)[K], double *red, double *out) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // warp trees in the accumulators' own precision (FP64 is a narrow pipe), warp
+    // totals widened to FP64 and added in a fixed order
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        double x = (double)v[k];
+        A x = v[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-        if (lane == 0) red[wid * K + k] = x;
+        if (lane == 0) red[wid * K + k] = (double)x;
     }
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
@@ -553,9 +572,19 @@ __device__ __forceinline__ void publish_and_tail(const Solve &s, int tile, int c
     const int per = (nb + chunks - 1) / chunks;
     if (threadIdx.x < chunks * K) {
         const int k = threadIdx.x % K, ch = threadIdx.x / K;
+        const double *src = s.partial + (int64_t)tile * s.bpt * K + k;
         double acc = 0.0;
         const int b1 = min(nb, (ch + 1) * per);
-        for (int b = ch * per; b < b1; ++b) acc += s.partial[((int64_t)tile * s.bpt + b) * K + k];
+        int b = ch * per;
+        // eight independent loads in flight, added in block order
+        for (; b + 8 <= b1; b += 8) {
+            double v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = src[(int64_t)(b + j) * K];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc += v[j];
+        }
+        for (; b < b1; ++b) acc += src[(int64_t)b * K];
         scratch[ch * K + k] = acc;
     }
     __syncthreads();
@@ -582,7 +611,7 @@ __device__ __forceinline__ void finish_pass(const Solve &s, int tile, int cur, c
 
 template <typename V, int T, int KIND>
 __global__ void __launch_bounds__(256) k_pass(Solve s, int cur) {
-    const int tile = blockIdx.y;
+    const int tile = launch_tile(s);
     if (s.tile_done[tile]) return;
     Dots<V, T> d;
     d.zero();
@@ -610,10 +639,13 @@ __global__ void __launch_bounds__(256) k_pass(Solve s, int cur) {
 // a torus wraps its indices.  The 13-point square applies that form twice.
 constexpr int SW = 128;
 
+// H: stencil reach in rows; XH: halo columns on each side of a strip (2 for both
+// kinds, so that strip starts stay 16-byte aligned for bulk row copies)
 template <int KIND>
 struct Strip {
     static constexpr int H = KIND == KIND_2D13_SQ ? 2 : 1;
-    static constexpr int W = SW - 2 * H;   // output columns per strip
+    static constexpr int XH = 2;
+    static constexpr int W = SW - 2 * XH;   // output columns per strip
 };
 
 // threads per lattice column: one thread holds all T columns of its lattice
@@ -816,10 +848,11 @@ __device__ __forceinline__ void stream_sweep(const Solve &s, int tile, int cur, 
     const int nx = s.op.nx, ny = s.op.ny;
     const bool per = s.op.periodic;
     const int xl = threadIdx.x / G, g = threadIdx.x - xl * G;
-    const int gx = strip * Strip<KIND>::W - H + xl;
+    constexpr int XH = Strip<KIND>::XH;
+    const int gx = strip * Strip<KIND>::W - XH + xl;
     bool inx;
     const int gxw = wrap_coord(gx, nx, per, inx);
-    const bool outx = xl >= H && xl < H + Strip<KIND>::W && gx < nx;
+    const bool outx = xl >= XH && xl < XH + Strip<KIND>::W && gx < nx;
     const int cb = tile * T + g * TS;
     const int64_t off = (int64_t)tile * s.op.n * T + g * TS;
     const V *const r = static_cast<const V *>(cur ? s.rbuf[1] : s.rbuf[0]) + off;
@@ -892,6 +925,7 @@ __device__ __forceinline__ void stream_sweep(const Solve &s, int tile, int cur, 
     // pending completes it.
 #pragma unroll
     for (int k = 0; k < PD - H; ++k) load_row(y + k, k);
+    const P sc = M::splat(op_scale<V>(s.op)), k2 = M::splat(op_kappa2<V>(s.op));
     int slot = 0;            // slot of row y
     for (; y < yend; ++y) {
         cp_async_wait<PD - 1 - H>();
@@ -904,9 +938,7 @@ __device__ __forceinline__ void stream_sweep(const Solve &s, int tile, int cur, 
             pw2 = pk;
         }
         const int slot_h = slot - H < 0 ? slot - H + PD : slot - H;   // slot of row y - H
-        const P sc = M::splat((V)s.op.scale);
         if constexpr (KIND == KIND_2D13_SQ) {
-            const P k2 = M::splat((V)s.op.kappa2);
             // u = Q1 p at (x, y-1): p row y-1 was shared last step
             if (y >= ys) {
                 P u = zero_pack<V, TS>();
@@ -932,7 +964,7 @@ __device__ __forceinline__ void stream_sweep(const Solve &s, int tile, int cur, 
             if (y - 1 >= ys && y - 1 < ye && outx) {
                 const int64_t gi = (int64_t)(y - 1) * nx + gx;
                 V dg = field_at<V>(s.op, gi);
-                if (s.op.mask) dg += (V)s.op.tau * (V)s.op.mask[gi];
+                if (s.op.mask) dg += op_tau<V>(s.op) * (V)s.op.mask[gi];
                 const P *row = ps + ((y - 1) & 1) * NT;
                 const P wk = M::mul(sc, diff5p<V, TS>(M::splat(dg), pw1, row[threadIdx.x - G], row[threadIdx.x + G], pw0, pw2));
                 emit(y - 1, slot_h, pw1, wk);
@@ -947,48 +979,302 @@ __device__ __forceinline__ void stream_sweep(const Solve &s, int tile, int cur, 
     __syncthreads();
 }
 
-// CTA sums of the sweep accumulators into cta[NDOT*T] (shared): per-thread partials,
-// then one thread per (dot, column) adds its SW lattice columns in a fixed order.
-// smem: >= SW*G*NDOT*TS words of V.  Ends with a barrier.
-template <typename V, int T, int G>
-__device__ __forceinline__ void stream_cta_sums(const StreamAcc<V, T / G> &acc, unsigned char *smem,
-                                                double *cta) {
-    constexpr int TS = T / G, K = NDOT * T;
-    V *part = reinterpret_cast<V *>(smem);
-    {
-        V *mine = part + threadIdx.x * NDOT * TS;
-#pragma unroll
-        for (int t = 0; t < TS; ++t) {
-            mine[0 * TS + t] = acc.rr.v[t];
-            mine[1 * TS + t] = acc.pw.v[t];
-            mine[2 * TS + t] = acc.rw.v[t];
-            mine[3 * TS + t] = acc.ww.v[t];
-            mine[4 * TS + t] = acc.vr[t];
-            mine[5 * TS + t] = acc.vw[t];
+// ------------------------------------------------------------------ bulk-copy rows
+// Rows of r, w, p move global -> shared as whole strip rows by the bulk copy
+// engine (cp.async.bulk, completion counted on an mbarrier per ring slot), issued
+// by one thread; per-thread 8..32-byte cp.async copies of the same rows keep the
+// load/store units and L1 busy and reach about two thirds of HBM bandwidth on
+// this access pattern, the bulk copies nearly all of it.
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+                 "r"(bytes) : "memory");
+}
+// dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
+    return t;
+}
+// wait for phase `parity` of the barrier; gives up after about a second (false)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    const unsigned a = smem_u32(bar);
+    uint64_t t0 = 0;
+    for (unsigned it = 0;; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((it & 63) == 0) {
+            const uint64_t t = global_ns();
+            if (it == 0) t0 = t;
+            else if (t - t0 > 1000000000ull) return false;
         }
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        const int dot = k / T, col = k - dot * T;
-        const int gg = col / TS, t = col - gg * TS;
-        double a = 0.0;
-        for (int xx = 0; xx < SW; ++xx) a += (double)part[(xx * G + gg) * NDOT * TS + dot * TS + t];
-        cta[k] = a;
+}
+
+constexpr int STREAM_PD_BULK = 8;   // ring depth of the bulk-copy sweep
+
+template <typename V, int T>
+constexpr size_t stream_bulk_smem_bytes() {
+    constexpr size_t pk = sizeof(Pack<V, T>);
+    constexpr size_t rows = (4 + 3 * STREAM_PD_BULK) * SW * pk + STREAM_PD_BULK * SW * sizeof(int);
+    constexpr size_t part = (size_t)SW * NDOT * T * sizeof(V);
+    constexpr size_t red = (size_t)SW * sizeof(double);
+    return rows > part ? (rows > red ? rows : red) : (part > red ? part : red);
+}
+
+// Host-side test of the bulk path's alignment rules: every strip row piece must
+// start on a 16-byte boundary and be a multiple of 16 bytes long, and a torus
+// wraps a strip at most once.  Row pieces start at column strip*W - XH (even) and
+// rows at y*nx: a pack of 16 or 32 bytes always qualifies, 8 or 24 bytes need an
+// even nx.
+inline bool stream_bulk_ok(int nx, int pack_bytes) {
+    if (nx < SW) return false;
+    if (pack_bytes % 16 == 0) return true;
+    return pack_bytes % 8 == 0 && nx % 2 == 0;
+}
+
+// The sweep of stream_sweep with rows of r, w, p arriving by bulk copies into a
+// ring shared by the CTA (slot rows [r | w | p] of SW packs).  Thread 0 issues
+// row y - H + PD into the slot of row y - H after the barrier that ends step y
+// (every thread has then finished reading it); each row completes one phase of
+// its slot's mbarrier (an arrival without bytes when the row is outside the grid
+// or past the segment).  Out-of-grid entries read as zero.  Colours still move by
+// per-thread cp.async (4 bytes a vertex, own columns only matter).  bars: PD
+// mbarriers in static shared memory.
+template <typename V, int T, int KIND, bool KEEPX>
+__device__ __forceinline__ void stream_sweep_bulk(const Solve &s, int tile, int cur, int strip, int ys,
+                                                  int ye, unsigned char *smem, uint64_t *bars,
+                                                  StreamAcc<V, T> &acc) {
+    constexpr int H = Strip<KIND>::H, XH = Strip<KIND>::XH, PD = STREAM_PD_BULK, NT = SW;
+    constexpr unsigned PB = sizeof(Pack<V, T>);
+    static_assert(PB == T * sizeof(V), "packs are unpadded rows of T values");
+    using P = Pack<V, T>;
+    using M = PackMath<V, T>;
+    P *const ps = reinterpret_cast<P *>(smem);
+    P *const us = ps + 2 * NT;
+    P *const ring = ps + 4 * NT;     // [PD][3][NT], shared by the CTA
+    int *const ringc = reinterpret_cast<int *>(ps + (4 + 3 * PD) * NT) + threadIdx.x;
+    const int nx = s.op.nx, ny = s.op.ny;
+    const bool per = s.op.periodic;
+    const int xl = threadIdx.x;
+    const int gx0 = strip * Strip<KIND>::W - XH;
+    const int gx = gx0 + xl;
+    bool inx;
+    const int gxw = wrap_coord(gx, nx, per, inx);
+    const bool outx = xl >= XH && xl < XH + Strip<KIND>::W && gx < nx;
+    const int cb = tile * T;
+    const int64_t off = (int64_t)tile * s.op.n * T;
+    const V *const r = static_cast<const V *>(cur ? s.rbuf[1] : s.rbuf[0]) + off;
+    const V *const w = static_cast<const V *>(cur ? s.wbuf[1] : s.wbuf[0]) + off;
+    const V *const p = static_cast<const V *>(cur ? s.pbuf[1] : s.pbuf[0]) + off;
+    P na, b;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        na.v[t] = -(V)s.alpha[cb + t];
+        b.v[t] = (V)s.beta[cb + t];
     }
+    P pw0 = zero_pack<V, T>(), pw1 = pw0, pw2 = pw0;   // p at rows y-2, y-1, y
+    P uw0 = pw0, uw1 = pw0, uw2 = pw0;                 // u at rows y-3, y-2, y-1
+    int y = ys - H;
+    const int yend = ye + H;
+    // column pieces of every row copy: [c0, c1) of the row, and on a torus the
+    // wrapped columns left of 0 (to slot offset 0) and right of nx - 1
+    const int c0 = gx0 < 0 ? 0 : gx0;
+    const int c1 = gx0 + SW > nx ? nx : gx0 + SW;
+    const int lw = per && gx0 < 0 ? -gx0 : 0;
+    const int rw = per && gx0 + SW > nx ? gx0 + SW - nx : 0;
+    const unsigned row_bytes = (unsigned)(c1 - c0 + lw + rw) * PB;
+
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < PD; ++k) mbar_init(&bars[k], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    auto issue = [&](int yr, int slot) {   // thread 0
+        bool iny;
+        const int gyw = wrap_coord(yr, ny, per, iny);
+        if (!iny || yr >= yend) {
+            mbar_arrive(&bars[slot]);
+            return;
+        }
+        mbar_arrive_tx(&bars[slot], 3 * row_bytes);
+        const int64_t re = (int64_t)gyw * nx * T;
+        const V *src[3] = {r + re, w + re, p + re};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            P *dst = ring + (slot * 3 + a) * NT;
+            bulk_g2s(dst + (c0 - gx0), src[a] + (int64_t)c0 * T, (unsigned)(c1 - c0) * PB, &bars[slot]);
+            if (lw) bulk_g2s(dst, src[a] + (int64_t)(nx - lw) * T, (unsigned)lw * PB, &bars[slot]);
+            if (rw) bulk_g2s(dst + (nx - gx0), src[a], (unsigned)rw * PB, &bars[slot]);
+        }
+    };
+    auto load_colour = [&](int yr, int slot) {
+        bool iny;
+        const int gyw = wrap_coord(yr, ny, per, iny);
+        const bool in = iny && inx && yr < yend;
+        const unsigned dc = smem_u32(ringc + slot * NT);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dc),
+                     "l"(s.colour + (in ? (int64_t)gyw * nx + gxw : 0)), "r"(in ? 4 : 0));
+        cp_async_commit();
+    };
+    auto emit = [&](int yo, int slot, const P &pk, const P &wk) {
+        const P *q = ring + slot * 3 * NT + xl;
+        const P rk = M::fma(na, q[NT], q[0]);
+        const int64_t e = ((int64_t)yo * nx + gx) * T;
+        V *rn = static_cast<V *>(cur ? s.rbuf[0] : s.rbuf[1]) + off;
+        V *wn = static_cast<V *>(cur ? s.wbuf[0] : s.wbuf[1]) + off;
+        V *pn = static_cast<V *>(cur ? s.pbuf[0] : s.pbuf[1]) + off;
+        *reinterpret_cast<P *>(rn + e) = rk;
+        *reinterpret_cast<P *>(pn + e) = pk;
+        *reinterpret_cast<P *>(wn + e) = wk;
+        if constexpr (KEEPX) {
+            V *x = static_cast<V *>(s.x) + off;
+            const P xo = *reinterpret_cast<const P *>(x + e);
+            *reinterpret_cast<P *>(x + e) = M::fma(M::neg(na), q[2 * NT], xo);
+        }
+        const int lc = ringc[slot * NT] - cb;
+        acc.rr = M::fma(rk, rk, acc.rr);
+        acc.pw = M::fma(pk, wk, acc.pw);
+        acc.rw = M::fma(rk, wk, acc.rw);
+        acc.ww = M::fma(wk, wk, acc.ww);
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            if (lc == t) {
+                acc.vr[t] += rk.v[t];
+                acc.vw[t] += wk.v[t];
+            }
+        }
+    };
+
+    // ring slot of row yr is (yr - y0) mod PD, its n-th fill completes phase n of the
+    // slot's barrier (parity bit kept per slot); see stream_sweep for the schedule
+    for (int k = 0; k < PD - H; ++k) {
+        if (threadIdx.x == 0) issue(y + k, k);
+        load_colour(y + k, k);
+    }
+    const P sc = M::splat(op_scale<V>(s.op)), k2 = M::splat(op_kappa2<V>(s.op));
+    int slot = 0;
+    unsigned parity = 0;
+    bool ok = true;
+    for (; y < yend; ++y) {
+        cp_async_wait<PD - 1 - H>();
+        ok &= mbar_wait(&bars[slot], (parity >> slot) & 1u);
+        parity ^= 1u << slot;
+        {
+            bool iny;
+            wrap_coord(y, ny, per, iny);
+            const bool in = iny && inx;
+            const P *q = ring + slot * 3 * NT + xl;
+            const P z = zero_pack<V, T>();
+            const P rv = in ? q[0] : z, wv = in ? q[NT] : z, pv = in ? q[2 * NT] : z;
+            const P pk = M::fma(b, pv, M::fma(na, wv, rv));
+            ps[(y & 1) * NT + threadIdx.x] = pk;
+            pw0 = pw1;
+            pw1 = pw2;
+            pw2 = pk;
+        }
+        const int slot_h = slot - H < 0 ? slot - H + PD : slot - H;   // slot of row y - H
+        if constexpr (KIND == KIND_2D13_SQ) {
+            if (y >= ys) {
+                P u = zero_pack<V, T>();
+                bool uin;
+                wrap_coord(y - 1, ny, per, uin);
+                if (uin && inx && xl >= 1 && xl < SW - 1) {
+                    const P *row = ps + ((y - 1) & 1) * NT;
+                    u = diff5p<V, T>(k2, pw1, row[threadIdx.x - 1], row[threadIdx.x + 1], pw0, pw2);
+                }
+                us[((y - 1) & 1) * NT + threadIdx.x] = u;
+                uw0 = uw1;
+                uw1 = uw2;
+                uw2 = u;
+            }
+            if (y - 2 >= ys && y - 2 < ye && outx) {
+                const P *row = us + ((y - 2) & 1) * NT;
+                const P wk = M::mul(sc, diff5p<V, T>(k2, uw1, row[threadIdx.x - 1], row[threadIdx.x + 1], uw0, uw2));
+                emit(y - 2, slot_h, pw0, wk);
+            }
+        } else {
+            if (y - 1 >= ys && y - 1 < ye && outx) {
+                const int64_t gi = (int64_t)(y - 1) * nx + gx;
+                V dg = field_at<V>(s.op, gi);
+                if (s.op.mask) dg += op_tau<V>(s.op) * (V)s.op.mask[gi];
+                const P *row = ps + ((y - 1) & 1) * NT;
+                const P wk = M::mul(sc, diff5p<V, T>(M::splat(dg), pw1, row[threadIdx.x - 1], row[threadIdx.x + 1], pw0, pw2));
+                emit(y - 1, slot_h, pw1, wk);
+            }
+        }
+        load_colour(y - H + PD, slot_h);
+        slot = slot + 1 == PD ? 0 : slot + 1;
+        __syncthreads();
+        if (threadIdx.x == 0) issue(y - H + PD, slot_h);
+    }
+    cp_async_wait<0>();
+    if (!ok) set_status(s.status, DEV_TIMEOUT);
     __syncthreads();
 }
 
-template <typename V, int T, int G, int KIND, bool KEEPX>
+// CTA sums of the sweep accumulators into cta[NDOT*T] (shared), dot-major
+// (k = dot * T + column).  smem: >= (blockDim / 32) * NDOT * T doubles.  Ends with a
+// barrier.
+template <typename V, int T, int G>
+__device__ __forceinline__ void stream_cta_sums(const StreamAcc<V, T / G> &acc, unsigned char *smem,
+                                                double *cta) {
+    static_assert(G == 1, "one thread per lattice column");
+    V flat[NDOT * T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        flat[0 * T + t] = acc.rr.v[t];
+        flat[1 * T + t] = acc.pw.v[t];
+        flat[2 * T + t] = acc.rw.v[t];
+        flat[3 * T + t] = acc.ww.v[t];
+        flat[4 * T + t] = acc.vr[t];
+        flat[5 * T + t] = acc.vw[t];
+    }
+    block_sum_to<V, NDOT * T>(flat, reinterpret_cast<double *>(smem), cta);
+}
+
+template <typename V, int T, int G, int KIND, bool KEEPX, bool BULK>
 __global__ void __launch_bounds__(SW * G, stream_min_blocks_t<V, T>()) k_stream2d(Solve s, int cur) {
     constexpr int K = NDOT * T;
-    const int tile = blockIdx.y;
+    const int tile = launch_tile(s);
     if (s.tile_done[tile]) return;
     extern __shared__ __align__(16) unsigned char smem[];
     const int strip = blockIdx.x % s.strips, sg = blockIdx.x / s.strips;
     const int ys = sg * s.seg, ye = min(ys + s.seg, s.op.ny);
     StreamAcc<V, T / G> acc;
     acc.zero();
-    stream_sweep<V, T, G, KIND, KEEPX>(s, tile, cur, strip, ys, ye, smem, acc);
+    if constexpr (BULK) {
+        static_assert(G == 1, "bulk rows: one thread per lattice column");
+        __shared__ uint64_t bars[STREAM_PD_BULK];
+        stream_sweep_bulk<V, T, KIND, KEEPX>(s, tile, cur, strip, ys, ye, smem, bars, acc);
+    } else {
+        stream_sweep<V, T, G, KIND, KEEPX>(s, tile, cur, strip, ys, ye, smem, acc);
+    }
     __shared__ double cta[K];
     stream_cta_sums<V, T, G>(acc, smem, cta);
     publish_and_tail<K>(s, tile, cur, cta, reinterpret_cast<double *>(smem));
@@ -1022,7 +1308,7 @@ __global__ void __launch_bounds__(P3T, stream3d_min_blocks<V, T>()) k_stream3d(S
     constexpr int K = NDOT * T, PD = STREAM_PD, H = 1;
     using P = Pack<V, T>;
     using M = PackMath<V, T>;
-    const int tile = blockIdx.y;
+    const int tile = launch_tile(s);
     if (s.tile_done[tile]) return;
     extern __shared__ __align__(16) unsigned char smem[];
     P *const ps = reinterpret_cast<P *>(smem);                    // 2 planes
@@ -1074,7 +1360,7 @@ __global__ void __launch_bounds__(P3T, stream3d_min_blocks<V, T>()) k_stream3d(S
         cp_async_commit();
     };
     P pw0 = zero_pack<V, T>(), pw1 = pw0, pw2 = pw0;   // p at planes z-2, z-1, z
-    const P sc = M::splat((V)s.op.scale);
+    const P sc = M::splat(op_scale<V>(s.op));
     // ring slot of plane zr is (zr - z0) mod PD (see the 2D sweep for the schedule)
 #pragma unroll
     for (int k = 0; k < PD - H; ++k) load_plane(z + k, k);
@@ -1093,7 +1379,7 @@ __global__ void __launch_bounds__(P3T, stream3d_min_blocks<V, T>()) k_stream3d(S
         if (z - 1 >= zs && z - 1 < ze && out) {
             const int64_t gi = (int64_t)(z - 1) * plane + (int64_t)gy * nx + gx;
             V dg = field_at<V>(s.op, gi);
-            if (s.op.mask) dg += (V)s.op.tau * (V)s.op.mask[gi];
+            if (s.op.mask) dg += op_tau<V>(s.op) * (V)s.op.mask[gi];
             const P *pl = ps + ((z - 1) & 1) * P3T;
             const P c = pw1;
             const P h = M::add(M::add(M::sub(c, pl[threadIdx.x - 1]), M::sub(c, pl[threadIdx.x + 1])),
@@ -1131,28 +1417,19 @@ __global__ void __launch_bounds__(P3T, stream3d_min_blocks<V, T>()) k_stream3d(S
     }
     cp_async_wait<0>();
     __syncthreads();
-    // CTA sums: per-thread partials -> shared, one thread per (dot, column) adds them
-    V *part = reinterpret_cast<V *>(smem);
-    {
-        V *mine = part + threadIdx.x * NDOT * T;
+    // CTA sums (warp trees, then the warps in a fixed order)
+    V flat[K];
 #pragma unroll
-        for (int t = 0; t < T; ++t) {
-            mine[0 * T + t] = acc.rr.v[t];
-            mine[1 * T + t] = acc.pw.v[t];
-            mine[2 * T + t] = acc.rw.v[t];
-            mine[3 * T + t] = acc.ww.v[t];
-            mine[4 * T + t] = acc.vr[t];
-            mine[5 * T + t] = acc.vw[t];
-        }
+    for (int t = 0; t < T; ++t) {
+        flat[0 * T + t] = acc.rr.v[t];
+        flat[1 * T + t] = acc.pw.v[t];
+        flat[2 * T + t] = acc.rw.v[t];
+        flat[3 * T + t] = acc.ww.v[t];
+        flat[4 * T + t] = acc.vr[t];
+        flat[5 * T + t] = acc.vw[t];
     }
-    __syncthreads();
     __shared__ double cta[K];
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        double a = 0.0;
-        for (int th = 0; th < P3T; ++th) a += (double)part[th * NDOT * T + k];
-        cta[k] = a;
-    }
-    __syncthreads();
+    block_sum_to<V, K>(flat, reinterpret_cast<double *>(smem), cta);
     publish_and_tail<K>(s, tile, cur, cta, reinterpret_cast<double *>(smem));
 }
 
@@ -1200,6 +1477,6 @@ static int dispatch(int precision, int T, int kind, A &&...args) {
 template <typename V>
 int iteration_launch(const Solve &s, int cur, cudaStream_t st);
 template <typename V>
-int iteration_occupancy(int T, int kind, int *occ);
+int iteration_occupancy(int T, int kind, bool bulk, int *occ);
 
 }  // namespace ld

@@ -8,13 +8,23 @@ namespace ld {
 template <typename V, int T, int KIND>
 struct IterLauncher {
     static int run(const Solve &s, int cur, cudaStream_t st) {
-        dim3 grid(s.bpt, s.ntiles);
+        const int ts = s.tstride > 0 ? s.tstride : 1;
+        const int nt = s.tile0 < s.ntiles ? (s.ntiles - s.tile0 + ts - 1) / ts : 0;
+        if (nt == 0) return 0;
+        dim3 grid(s.bpt, nt);
         if constexpr (KIND == KIND_2D5 || KIND == KIND_2D13_SQ) {
             constexpr int G = stream_groups<V, T>();
-            if (s.keep_x0)
-                k_stream2d<V, T, G, KIND, true><<<grid, SW * G, stream_smem_bytes<V, T, G>(), st>>>(s, cur);
-            else
-                k_stream2d<V, T, G, KIND, false><<<grid, SW * G, stream_smem_bytes<V, T, G>(), st>>>(s, cur);
+            constexpr size_t sm = stream_smem_bytes<V, T, G>(), smb = stream_bulk_smem_bytes<V, T>();
+            if (s.bulk) {
+                if (s.keep_x0)
+                    k_stream2d<V, T, 1, KIND, true, true><<<grid, SW, smb, st>>>(s, cur);
+                else
+                    k_stream2d<V, T, 1, KIND, false, true><<<grid, SW, smb, st>>>(s, cur);
+            } else if (s.keep_x0) {
+                k_stream2d<V, T, G, KIND, true, false><<<grid, SW * G, sm, st>>>(s, cur);
+            } else {
+                k_stream2d<V, T, G, KIND, false, false><<<grid, SW * G, sm, st>>>(s, cur);
+            }
         } else if constexpr (KIND == KIND_3D7) {
             if (s.keep_x0)
                 k_stream3d<V, T, true><<<grid, P3T, stream3d_smem_bytes<V, T>(), st>>>(s, cur);
@@ -30,17 +40,24 @@ struct IterLauncher {
 template <typename V, int T, int KIND>
 struct OccLauncher {
     // resident CTAs per SM of the iteration kernels (the smaller of the two phases)
-    static int run(int *out) {
+    static int run(int *out, bool bulk) {
         int a = 0, b = 0;
         if constexpr (KIND == KIND_2D5 || KIND == KIND_2D13_SQ) {
             constexpr int G = stream_groups<V, T>();
-            constexpr size_t sm = stream_smem_bytes<V, T, G>();
-            if (cudaFuncSetAttribute(k_stream2d<V, T, G, KIND, false>,
+            constexpr size_t sm = stream_smem_bytes<V, T, G>(), smb = stream_bulk_smem_bytes<V, T>();
+            if (cudaFuncSetAttribute(k_stream2d<V, T, G, KIND, false, false>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
-                cudaFuncSetAttribute(k_stream2d<V, T, G, KIND, true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+                cudaFuncSetAttribute(k_stream2d<V, T, G, KIND, true, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+                cudaFuncSetAttribute(k_stream2d<V, T, 1, KIND, false, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb) != cudaSuccess ||
+                cudaFuncSetAttribute(k_stream2d<V, T, 1, KIND, true, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb) != cudaSuccess)
                 return (int)cudaGetLastError();
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_stream2d<V, T, G, KIND, true>, SW * G, sm);
+            if (bulk)
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_stream2d<V, T, 1, KIND, true, true>, SW, smb);
+            else
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_stream2d<V, T, G, KIND, true, false>, SW * G, sm);
         } else if constexpr (KIND == KIND_3D7) {
             constexpr size_t sm = stream3d_smem_bytes<V, T>();
             if (cudaFuncSetAttribute(k_stream3d<V, T, false>,
@@ -64,8 +81,8 @@ int iteration_launch(const Solve &s, int cur, cudaStream_t st) {
 }
 
 template <typename V>
-int iteration_occupancy(int T, int kind, int *occ) {
-    return dispatch_v<V, OccLauncher>(T, kind, occ);
+int iteration_occupancy(int T, int kind, bool bulk, int *occ) {
+    return dispatch_v<V, OccLauncher>(T, kind, occ, bulk);
 }
 
 }  // namespace ld

@@ -36,6 +36,7 @@ struct Operator {
     double kappa2;
     double tau;
     double scale;
+    float kappa2_f, tau_f, scale_f;   // FP32 copies (set_f32_coefs), read by FP32 kernels
     const double *field_d;   // kappa2 field base values, FP64 copy
     const float *field_f;    // FP32 copy
     const uint8_t *mask;     // observation mask (or nullptr)
@@ -44,6 +45,13 @@ struct Operator {
     const double *val_d;
     const float *val_f;
 };
+
+// FP32 copies of the operator's coefficients, so that FP32 kernels convert nothing
+inline void set_f32_coefs(Operator &op) {
+    op.kappa2_f = (float)op.kappa2;
+    op.tau_f = (float)op.tau;
+    op.scale_f = (float)op.scale;
+}
 
 // Status codes written by kernels into the device status word.
 enum { DEV_OK = 0, DEV_NOTSPD = 4, DEV_NUMERIC = 6, DEV_TIMEOUT = 7 };
@@ -57,6 +65,9 @@ struct Solve {
     int nshift;            // N
     int bpt;               // CTAs per tile (grid engine)
     int strips, seg;       // 2D kinds: lattice strips per tile, rows per CTA segment
+    int bulk;              // 2D kinds: rows arrive by bulk (TMA) copies (alignment permits)
+    int tile0, tstride;    // grid engine: a launch covers tiles tile0, tile0 + tstride, ...
+                           // (grid.y of them; tstride 0 reads as 1)
     int precision;         // 0 fp64, 1 mixed
     int keep_x0;
     double tol;

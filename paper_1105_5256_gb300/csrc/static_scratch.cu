@@ -147,6 +147,7 @@ extern "C" ld_status ld_logdet_static(const ld_matrix *Q, const int32_t *colour,
     s.op.kappa2 = Q->kappa2;
     s.op.tau = 0.0;
     s.op.scale = scale;
+    set_f32_coefs(s.op);
     s.T = T;
     s.ntiles = C;
     s.ncols = C;

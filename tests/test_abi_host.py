@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported(lib):
     assert len(syms) >= 20
     for s in syms:
         assert hasattr(lib, s), s
-    assert lib.ld_abi_version() == 1
+    assert lib.ld_abi_version() == 2
 
 
 @pytest.mark.parametrize("kind,dims,per,d", [
