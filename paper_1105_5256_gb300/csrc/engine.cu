@@ -599,7 +599,10 @@ int engine_plan(Solve &s) {
     const int oe = s.precision == 0 ? iteration_occupancy<double>(s.T, s.op.kind, s.bulk != 0, &occ)
                                     : iteration_occupancy<float>(s.T, s.op.kind, s.bulk != 0, &occ);
     if (oe != 0 || occ < 1) occ = 1;
-    const int64_t target = (int64_t)sms * occ;   // exactly one resident wave
+    // one resident wave; with several tiles (tile groups run concurrently on their own
+    // streams) 1.5 waves, so that CTAs of one group fill the gaps of another
+    int64_t target = (int64_t)sms * occ;
+    if (s.ntiles >= 2) target = target * 3 / 2;
     s.strips = 1;
     s.seg = 1;
     if (s.op.kind == KIND_2D5 || s.op.kind == KIND_2D13_SQ) {
