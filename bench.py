@@ -196,6 +196,63 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_field3d(args):
+    """Secondary workload: Dirichlet 256^3, 7-point, seeded kappa^2 field, distance-6
+    colouring, N = 32, tol 1e-6, mixed precision; one evaluation = log det and its
+    derivative with respect to the field's scale c (kappa^2(s) = c kappa0^2(s))."""
+    import torch
+    import paper_1105_5256_gb300 as L
+    torch.cuda.set_device(0)
+    L.library(build_if_missing=True)
+    dims = (256, 256, 256)
+    n = dims[0] * dims[1] * dims[2]
+    field = synth.kappa2_field(5, dims)
+    ctx = L.ld_create(L.grid_matrix(L.LD_STENCIL_3D7, dims, 1.0, kappa2_field=field), 6, 32, 1e-6,
+                      L.options(precision=L.LD_MIXED, tile_width=args.tile_width))
+    for _ in range(args.warmup):
+        L.ld_logdet_grad(ctx, [L.LD_P_KAPPA2])
+    clocks = Clocks()
+    clocks.start()
+    t0 = time.perf_counter()
+    dev_ms = iter_ms = 0.0
+    tile_iters = passes = launches = 0
+    for _ in range(args.steps):
+        v, g, info = L.ld_logdet_grad(ctx, [L.LD_P_KAPPA2])
+        dev_ms += info["ms"]
+        iter_ms += info["iter_ms"]
+        tile_iters += info["tile_iters"]
+        passes += info["iters"]
+        launches += info["gpu_launches"]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    T = info["tile_width"]
+    ntiles = (info["n_colours"] + T - 1) // T
+    # per tile-pass: r, w, p read and written, x read and written (gradient mode); per
+    # pass: the colour and the FP32 field, once
+    alg = (8 * n * T * 4) * tile_iters + (4 + 4) * n * passes
+    peak, src = peak_hbm()
+    achieved = alg / (iter_ms / 1e3) / 1e9
+    line = {"metric": "log-det+grad evals/sec (Dirichlet 256^3, 7-point, kappa^2 field, d=6, N=32)",
+            "value": args.steps / (dev_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 vectors / f64 scalars",
+            "data": "synthetic (seeded kappa^2 field)",
+            "config": {"workload": "Dirichlet 256^3, 7-point, kappa^2 field, d=6, N=32, tol 1e-6, grad c",
+                       "n": n, "n_colours": info["n_colours"], "tile_width": T,
+                       "passes_per_eval": passes / args.steps},
+            "clocks": clk,
+            "e2e": {"value": args.steps / wall, "unit": UNIT, "h2d_bytes_per_step": 16,
+                    "d2h_bytes_per_step": 16},
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "kernel": "fused CG pass (k_stream3d)", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "algorithmic_bytes_per_launch": 8 * n * T * 4 * ntiles + 8 * n,
+                         "peak_source": src},
+            "logdet": v, "grad_c": float(g[0])}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import torch
     import paper_1105_5256_gb300 as L
@@ -395,7 +452,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=BATCH, help="kappa^2 values per step")
     ap.add_argument("--tile-width", type=int, default=0, help="probing vectors per tile (0 = auto)")
-    ap.add_argument("--workload", default="matern1024", choices=["matern1024", "batch256"])
+    ap.add_argument("--workload", default="matern1024", choices=["matern1024", "batch256", "field3d256"])
     ap.add_argument("--fp64-sample", type=int, default=2,
                     help="draws also evaluated in the plain FP64 form (mixed precision runs)")
     ap.add_argument("--kappa2", type=float, default=0.0,
@@ -405,6 +462,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch256":
         run_batch(args)
+    elif args.workload == "field3d256":
+        run_field3d(args)
     else:
         run_ours(args)
 
