@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define LD_ABI_VERSION 2
+#define LD_ABI_VERSION 3
 
 typedef struct ld_ctx ld_ctx;
 
@@ -97,6 +97,14 @@ typedef struct {
     const int32_t *colouring; /* optional host colouring (n ints >= 0); NULL = greedy */
     int32_t engine;           /* 0 auto, 1 multi-CTA grid engine, 2 one-CTA-per-tile engine */
     int32_t chunk_iters;      /* iterations per captured CUDA graph chunk; 0 = auto */
+    double reliable_delta;    /* > 0: reliable-update residual replacement (grid engine).  The
+                                 seed solution is split into an FP64 part x_hi and a vector-
+                                 precision correction x_lo that the pass updates; whenever a
+                                 column's recursive residual norm falls below reliable_delta
+                                 times its largest norm since the last replacement, x_hi +=
+                                 x_lo, x_lo = 0 and every active tile's residual is replaced
+                                 by v - Q x_hi formed with FP64 arithmetic.  Keeps x0 on the
+                                 device (as keep_x0).  0 = off. */
 } ld_options;
 
 typedef struct {
@@ -115,6 +123,10 @@ typedef struct {
     int64_t gpu_launches;     /* kernels this call launched (graph nodes counted) */
     int32_t bulk_rows;        /* grid engine on a 2D lattice: 1 when lattice rows move by
                                  bulk (TMA) copies, 0 by per-thread copies; -1 otherwise */
+    int32_t reliable_updates; /* residual replacements this call made */
+    double rel_resid_max;     /* when x0 is kept (keep_x0, a gradient or reliable_delta > 0):
+                                 max over the call's columns of ||v_c - Q x_c|| / ||v_c||, the
+                                 true seed residual formed in FP64; -1 otherwise */
 } ld_info;
 
 /* ABI version (LD_ABI_VERSION).  Never fails. */

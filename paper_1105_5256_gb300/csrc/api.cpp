@@ -99,6 +99,7 @@ struct ld_ctx {
     // device
     DevBuf d_colour, d_field_d, d_field_f, d_mask, d_rowptr, d_colidx, d_val_d, d_val_f;
     DevBuf d_r[2], d_w[2], d_p[2], d_x;
+    DevBuf d_xhi, d_norm2;   // reliable updates: FP64 seed solution part; residual norms
     DevBuf d_colscal;  // 8 double arrays [ncols]
     DevBuf d_colint;   // 2 int arrays [ncols]
     DevBuf d_shift;    // 4 double2 arrays [ncols*N] + uint8 [ncols*N]
@@ -383,6 +384,25 @@ ld_status run_solve(ld_ctx *c, int cb, int ce, bool keep_x0, double out[2], ld_i
     int64_t launches = 0;
     int iters = 0;
     float ms = 0.f;
+    // reliable updates (grid engine): x kept as x_hi (FP64) + x_lo, residual replaced
+    // by v - Q x_hi whenever a column's residual norm fell by reliable_delta
+    const bool ru = c->opt.reliable_delta > 0.0 && c->engine == 1;
+    if (ru) keep_x0 = true;
+    if (ru && !c->d_xhi.p) CUDA_TRY(c->d_xhi.alloc((size_t)c->ntiles * c->n * c->T * sizeof(double)));
+    if (keep_x0 && !c->d_norm2.p) CUDA_TRY(c->d_norm2.alloc((size_t)c->ncols * sizeof(double)));
+    double *want_xhi = ru ? c->d_xhi.as<double>() : nullptr;
+    if (c->s.xhi != want_xhi) {
+        c->s.xhi = want_xhi;
+        invalidate_graph(c);
+    }
+    if (ru) CUDA_TRY(cudaMemsetAsync(c->d_xhi.p, 0, c->d_xhi.bytes, c->stream));
+    int updates = 0;
+    std::vector<double> rmax, h_rho(c->ncols), h_norm2(c->ncols);
+    std::vector<int32_t> h_act(c->ncols);
+    if (ru) {
+        rmax.assign(c->ncols, 0.0);
+        for (int col = cb; col < ce; ++col) rmax[col] = std::sqrt(c->class_size[col]);
+    }
     if (keep_x0 && !c->d_x.p) {
         const size_t vb = (size_t)c->ntiles * c->n * c->T * (c->opt.precision == LD_FP64 ? 8 : 4);
         CUDA_TRY(c->d_x.alloc(vb));
@@ -424,18 +444,42 @@ ld_status run_solve(ld_ctx *c, int cb, int ce, bool keep_x0, double out[2], ld_i
             done_iters += c->chunk;
             CUDA_TRY(cudaMemcpyAsync(c->h_pinned, c->s.remaining, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
             CUDA_TRY(cudaMemcpyAsync(c->h_pinned + 1, c->s.status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+            if (ru) {
+                CUDA_TRY(cudaMemcpyAsync(h_rho.data(), c->s.rho, c->ncols * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+                CUDA_TRY(cudaMemcpyAsync(h_act.data(), c->s.col_active, c->ncols * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+            }
             CUDA_TRY(cudaStreamSynchronize(c->stream));
             float e = 0.f;
             CUDA_TRY(cudaEventElapsedTime(&e, c->ev2, c->ev3));
             iter_ms += e;
             if (c->h_pinned[0] <= 0 || c->h_pinned[1] != 0 || done_iters >= max_iter) break;
+            if (ru) {
+                // chunks hold an even number of passes: the next pass reads set 0, which
+                // holds r_k beside x_k = x_hi + x_lo
+                bool fire = false;
+                for (int col = cb; col < ce && !fire; ++col)
+                    fire = h_act[col] && std::sqrt(h_rho[col]) < c->opt.reliable_delta * rmax[col];
+                if (fire) {
+                    ENGINE_TRY(ld::engine_true_residual(c->s, 0, cb, ce, 1, c->d_norm2.as<double>(), c->stream));
+                    launches += 3;
+                    ++updates;
+                    CUDA_TRY(cudaMemcpyAsync(h_norm2.data(), c->d_norm2.p, c->ncols * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+                    CUDA_TRY(cudaStreamSynchronize(c->stream));
+                    for (int col = cb; col < ce; ++col) rmax[col] = std::sqrt(h_norm2[col]);
+                }
+            }
         }
     }
     const int dev_status = c->h_pinned[1];
     const int remaining = c->h_pinned[0];
+    double rel_resid = -1.0;
     if (c->s.keep_x0) {
         ENGINE_TRY(ld::engine_flush_x(c->s, c->stream));
         launches += 1;
+        // true seed residuals (folding x_lo into x_hi first under reliable updates)
+        ENGINE_TRY(ld::engine_true_residual(c->s, 0, cb, ce, 0, c->d_norm2.as<double>(), c->stream));
+        launches += ru ? 3 : 2;
+        CUDA_TRY(cudaMemcpyAsync(h_norm2.data(), c->d_norm2.p, c->ncols * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     }
     ENGINE_TRY(ld::engine_finish(c->s, cb, ce, c->stream));
     launches += 1;
@@ -458,7 +502,17 @@ ld_status run_solve(ld_ctx *c, int cb, int ce, bool keep_x0, double out[2], ld_i
     else if (dev_status != 0) st = fail(LD_ECUDA, "device status %d", dev_status);
     else if (remaining > 0) st = fail(LD_ENOTCONV, "%d tiles not converged after %d iterations", remaining, iters);
     else if (!std::isfinite(out[0])) st = fail(LD_ENUMERIC, "non-finite log det");
+    if (c->s.keep_x0) {
+        rel_resid = 0.0;
+        for (int col = cb; col < ce; ++col)
+            if (c->class_size[col] > 0)
+                rel_resid = std::max(rel_resid, std::sqrt(h_norm2[col] / c->class_size[col]));
+    }
     fill_info(c, info, st, iters, ms, launches, iter_ms, tile_iters);
+    if (info) {
+        info->reliable_updates = updates;
+        info->rel_resid_max = rel_resid;
+    }
     if (st == LD_OK) {
         c->have_x0 = keep_x0;
         c->solved = true;
@@ -611,6 +665,8 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
     if (opt.max_iter < 0) return fail(LD_EINVAL, "max_iter must be >= 0");
     if (opt.engine < 0 || opt.engine > 2) return fail(LD_EINVAL, "engine must be 0, 1 or 2");
     if (opt.chunk_iters < 0 || opt.chunk_iters > 4096) return fail(LD_EINVAL, "chunk_iters out of range");
+    if (!(opt.reliable_delta >= 0.0 && opt.reliable_delta < 1.0))
+        return fail(LD_EINVAL, "reliable_delta must be in [0, 1)");
 
     ld_ctx *c = new (std::nothrow) ld_ctx();
     if (!c) return fail(LD_ENOMEM, "host allocation");

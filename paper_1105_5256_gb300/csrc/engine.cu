@@ -435,6 +435,68 @@ __global__ void k_apply(Operator op, int ntiles, const V *x, V *y) {
     }
 }
 
+// ------------------------------------------------------------------ reliable updates
+// Residual replacement for mixed precision: the seed solution is x_hi (FP64) + x_lo
+// (vector precision, the pass's running correction).  Folding moves x_lo into x_hi;
+// the true residual v - Q x is then formed with FP64 arithmetic throughout.
+template <typename V, int T>
+__global__ void k_fold_x(Solve s) {
+    const int64_t total = (int64_t)s.ntiles * s.op.n * T;
+    V *xl = static_cast<V *>(s.x);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        s.xhi[e] += (double)xl[e];
+        xl[e] = (V)0;
+    }
+}
+
+template <typename V, int T>
+struct LoadWiden {   // an FP64 view of a vector-precision block (or of x_hi itself)
+    const V *p;
+    const double *d;
+    __device__ __forceinline__ void operator()(int64_t j, double (&o)[T]) const {
+#pragma unroll
+        for (int t = 0; t < T; ++t) o[t] = d ? d[j * T + t] : (double)p[j * T + t];
+    }
+};
+
+// grid (blocks, ntiles): one tile per blockIdx.y; per-column sums by block reduction
+template <typename V, int T, int KIND>
+__global__ void __launch_bounds__(256) k_true_residual(Solve s, int set, int cb, int ce, int replace,
+                                                        double *norm2) {
+    const int tile = blockIdx.y;
+    const int64_t n = s.op.n;
+    const int64_t off = (int64_t)tile * n * T;
+    LoadWiden<V, T> ld;
+    ld.p = static_cast<const V *>(s.x) + off;
+    ld.d = s.xhi ? s.xhi + off : nullptr;
+    V *r = static_cast<V *>(set ? s.rbuf[1] : s.rbuf[0]) + off;
+    const bool write = replace && !s.tile_done[tile];
+    double acc[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t) acc[t] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double w[T], self[T];
+        apply_row<double, T, KIND>(s.op, i, ld, w, self);
+        const int col = s.colour[i];
+        V out[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const int c = tile * T + t;
+            const double v = (col == c && c >= cb && c < ce) ? 1.0 : 0.0;
+            const double res = (c >= cb && c < ce) ? v - w[t] : 0.0;
+            acc[t] = fma(res, res, acc[t]);
+            out[t] = (V)res;
+        }
+        if (write) stpack<V, T>(r, i, out);
+    }
+    __shared__ double red[8 * T];
+    __shared__ double tot[T];
+    block_sum_to<double, T>(acc, red, tot);
+    if (threadIdx.x < T) atomicAdd(&norm2[tile * T + threadIdx.x], tot[threadIdx.x]);
+}
+
 // ------------------------------------------------------------------ gradient (backward)
 // g_eta = sum_c (E_eta v_c)^T x0_c = sum_i sum_j E_ij x0[i, colour(j)], E = dQ/d eta.
 // E per parameter id: kappa2 -> scale*diag(field or 1) (grid 5/7-pt), 2*scale*Q1 (13-pt);
@@ -442,8 +504,9 @@ __global__ void k_apply(Operator op, int ntiles, const V *x, V *y) {
 template <typename V>
 __device__ __forceinline__ double x0_at(const Solve &s, int64_t i, int c) {
     const int tile = c / s.T, lane = c - tile * s.T;
-    const V *x = static_cast<const V *>(s.x);
-    return (double)x[((int64_t)tile * s.op.n + i) * s.T + lane];
+    const int64_t e = ((int64_t)tile * s.op.n + i) * s.T + lane;
+    if (s.xhi) return s.xhi[e];
+    return (double)static_cast<const V *>(s.x)[e];
 }
 
 template <typename V>
@@ -575,6 +638,28 @@ struct InitLauncher {
 };
 
 template <typename V, int T, int KIND>
+struct ResidualLauncher {
+    static int run(const Solve &s, int set, int cb, int ce, int replace, double *norm2, cudaStream_t st) {
+        int e = (int)cudaMemsetAsync(norm2, 0, (size_t)s.ncols * sizeof(double), st);
+        if (e) return e;
+        if (s.xhi) {
+            const int64_t total = (int64_t)s.ntiles * s.op.n * T;
+            int blocks = (int)((total + 255) / 256);
+            if (blocks > 152 * 16) blocks = 152 * 16;
+            if (blocks < 1) blocks = 1;
+            k_fold_x<V, T><<<blocks, 256, 0, st>>>(s);
+            e = (int)cudaGetLastError();
+            if (e) return e;
+        }
+        int bx = (int)((s.op.n + 255) / 256);
+        if (bx > 152 * 8) bx = 152 * 8;
+        if (bx < 1) bx = 1;
+        k_true_residual<V, T, KIND><<<dim3(bx, s.ntiles), 256, 0, st>>>(s, set, cb, ce, replace, norm2);
+        return (int)cudaGetLastError();
+    }
+};
+
+template <typename V, int T, int KIND>
 struct ApplyLauncher {
     static int run(const Operator &op, int ntiles, const void *x, void *y, cudaStream_t st) {
         const int64_t total = (int64_t)ntiles * op.n;
@@ -699,6 +784,12 @@ int engine_apply(const Operator &op, int precision, int T, int ntiles, const voi
                  void *stream) {
     return dispatch<ApplyLauncher>(precision, T, op.kind, op, ntiles, x, y,
                                    static_cast<cudaStream_t>(stream));
+}
+
+int engine_true_residual(const Solve &s, int set, int col_begin, int col_end, int replace,
+                         double *norm2_dev, void *stream) {
+    return dispatch<ResidualLauncher>(s.precision, s.T, s.op.kind, s, set, col_begin, col_end, replace,
+                                      norm2_dev, static_cast<cudaStream_t>(stream));
 }
 
 int engine_grad_params(const Solve &s, int nparam, const int *ids, double *out_dev, void *stream) {

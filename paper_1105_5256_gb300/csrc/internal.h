@@ -75,7 +75,9 @@ struct Solve {
     // CG state, two sets read/written alternately by consecutive passes:
     // set[k & 1] -> set[(k & 1) ^ 1]; each [ntiles][n][T] in the vector precision
     void *rbuf[2], *wbuf[2], *pbuf[2];
-    void *x;               // seed solution (gradient mode)
+    void *x;               // seed solution (gradient mode); with reliable updates, the
+                           // correction x_lo since the last residual replacement
+    double *xhi;           // reliable updates: FP64 part x_hi of the seed solution (or null)
     // per-column scalars (ncols)
     double *rho, *alpha, *beta, *alpha_prev, *beta_prev, *vnorm2, *pi0, *phi0;
     int32_t *col_active, *col_iters;
@@ -115,6 +117,11 @@ int engine_finish(const Solve &s, int col_begin, int col_end, void *stream);
 int engine_apply(const Operator &op, int precision, int T, int ntiles, const void *x, void *y,
                  void *stream);
 int engine_grad_params(const Solve &s, int nparam, const int *ids, double *out_dev, void *stream);
+// reliable updates: x_hi += x_lo, x_lo = 0 (all tiles); then with replace != 0 the active
+// tiles' residuals in set `set` become v - Q x_hi.  norm2_dev[ncols] (zeroed here) receives
+// ||v_c - Q x_c||^2 in FP64 for c in [col_begin, col_end), x = x_hi when present, else x.
+int engine_true_residual(const Solve &s, int set, int col_begin, int col_end, int replace,
+                         double *norm2_dev, void *stream);
 int engine_plan(Solve &s);   // sets bpt (and strips/seg); returns bpt
 const char *engine_error_string(int cuda_err);
 

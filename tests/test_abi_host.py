@@ -39,7 +39,7 @@ def test_every_declared_symbol_is_exported(lib):
     assert len(syms) >= 20
     for s in syms:
         assert hasattr(lib, s), s
-    assert lib.ld_abi_version() == 2
+    assert lib.ld_abi_version() == 3
 
 
 @pytest.mark.parametrize("kind,dims,per,d", [
@@ -121,3 +121,12 @@ def test_invalid_matrix_rejected_on_host(lib):
     with pytest.raises(L.LogDetError) as e:
         L.ld_grid_bounds(L.grid_matrix(om.KIND_2D13_SQ, (8, 8), 0.5, kappa2_field=np.ones(64)))
     assert e.value.status == L.LD_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("kw", [{"reliable_delta": 1.5}, {"reliable_delta": -0.1}, {"engine": 3},
+                                {"chunk_iters": -1}, {"precision": 7}])
+def test_invalid_options_rejected_before_any_device_work(lib, kw):
+    """Option checks run before the context touches the device (no GPU needed)."""
+    with pytest.raises(L.LogDetError) as e:
+        L.ld_create(L.grid_matrix(om.KIND_2D5, (8, 8), 0.5), 2, 8, 1e-8, L.options(**kw))
+    assert e.value.status == L.LD_EINVAL
