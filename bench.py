@@ -204,7 +204,7 @@ def run_field3d(args):
     import paper_1105_5256_gb300 as L
     torch.cuda.set_device(0)
     L.library(build_if_missing=True)
-    dims = (256, 256, 256)
+    dims = (args.side, args.side, args.side)
     n = dims[0] * dims[1] * dims[2]
     field = synth.kappa2_field(5, dims)
     ctx = L.ld_create(L.grid_matrix(L.LD_STENCIL_3D7, dims, 1.0, kappa2_field=field), 6, 32, 1e-6,
@@ -233,12 +233,12 @@ def run_field3d(args):
     alg = (8 * n * T * 4) * tile_iters + (4 + 4) * n * passes
     peak, src = peak_hbm()
     achieved = alg / (iter_ms / 1e3) / 1e9
-    line = {"metric": "log-det+grad evals/sec (Dirichlet 256^3, 7-point, kappa^2 field, d=6, N=32)",
+    line = {"metric": "log-det+grad evals/sec (Dirichlet %d^3, 7-point, kappa^2 field, d=6, N=32)" % args.side,
             "value": args.steps / (dev_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 vectors / f64 scalars",
             "data": "synthetic (seeded kappa^2 field)",
-            "config": {"workload": "Dirichlet 256^3, 7-point, kappa^2 field, d=6, N=32, tol 1e-6, grad c",
+            "config": {"workload": "Dirichlet %d^3, 7-point, kappa^2 field, d=6, N=32, tol 1e-6, grad c" % args.side,
                        "n": n, "n_colours": info["n_colours"], "tile_width": T,
                        "passes_per_eval": passes / args.steps},
             "clocks": clk,
@@ -453,6 +453,7 @@ def main():
     ap.add_argument("--batch", type=int, default=BATCH, help="kappa^2 values per step")
     ap.add_argument("--tile-width", type=int, default=0, help="probing vectors per tile (0 = auto)")
     ap.add_argument("--workload", default="matern1024", choices=["matern1024", "batch256", "field3d256"])
+    ap.add_argument("--side", type=int, default=256, help="field3d256 workload: grid side")
     ap.add_argument("--fp64-sample", type=int, default=2,
                     help="draws also evaluated in the plain FP64 form (mixed precision runs)")
     ap.add_argument("--kappa2", type=float, default=0.0,

@@ -100,6 +100,7 @@ struct ld_ctx {
     DevBuf d_colour, d_field_d, d_field_f, d_mask, d_rowptr, d_colidx, d_val_d, d_val_f;
     DevBuf d_r[2], d_w[2], d_p[2], d_x;
     DevBuf d_xhi, d_norm2;   // reliable updates: FP64 seed solution part; residual norms
+    DevBuf d_diag_d, d_diag_f;   // per-vertex diagonal term (field and/or mask models)
     DevBuf d_colscal;  // 8 double arrays [ncols]
     DevBuf d_colint;   // 2 int arrays [ncols]
     DevBuf d_shift;    // 4 double2 arrays [ncols*N] + uint8 [ncols*N]
@@ -298,6 +299,23 @@ void fill_operator(ld_ctx *c) {
     op.colidx = c->d_colidx.as<int32_t>();
     op.val_d = c->d_val_d.as<double>();
     op.val_f = c->d_val_f.as<float>();
+}
+
+// per-vertex diagonal coefficients of field / mask models (see Operator::diag_d)
+ld_status fill_diag(ld_ctx *c) {
+    Operator &op = c->s.op;
+    op.diag_d = nullptr;
+    op.diag_f = nullptr;
+    const bool grid = c->kind == LD_STENCIL_2D5 || c->kind == LD_STENCIL_3D7;
+    if (!grid || (!op.field_d && !op.mask)) return LD_OK;
+    if (!c->d_diag_d.p) {
+        CUDA_TRY(c->d_diag_d.alloc((size_t)c->n * sizeof(double)));
+        CUDA_TRY(c->d_diag_f.alloc((size_t)c->n * sizeof(float)));
+    }
+    op.diag_d = c->d_diag_d.as<double>();
+    op.diag_f = c->d_diag_f.as<float>();
+    ENGINE_TRY(ld::engine_fill_diag(op, c->d_diag_d.as<double>(), c->d_diag_f.as<float>(), c->stream));
+    return LD_OK;
 }
 
 void invalidate_graph(ld_ctx *c) {
@@ -796,6 +814,7 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
 
     Solve &s = c->s;
     fill_operator(c);
+    if (ld_status st = fill_diag(c)) return st;
     s.T = c->T;
     s.ntiles = c->ntiles;
     s.ncols = C;
@@ -861,6 +880,7 @@ ld_status ld_set_params(ld_ctx *c, double kappa2, double tau, double scale) {
     c->tau = tau;
     c->scale = scale;
     fill_operator(c);
+    if (ld_status st = fill_diag(c)) return st;
     invalidate_graph(c);
     c->solved = false;
     c->have_x0 = false;

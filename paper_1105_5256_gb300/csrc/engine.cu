@@ -435,6 +435,17 @@ __global__ void k_apply(Operator op, int ntiles, const V *x, V *y) {
     }
 }
 
+// ------------------------------------------------------------------ diagonal coefficients
+__global__ void k_fill_diag(Operator op, double *dd, float *df) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < op.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double d = op.field_d ? op.kappa2 * op.field_d[i] : op.kappa2;
+        if (op.mask) d += op.tau * (double)op.mask[i];
+        dd[i] = d;
+        df[i] = (float)d;
+    }
+}
+
 // ------------------------------------------------------------------ reliable updates
 // Residual replacement for mixed precision: the seed solution is x_hi (FP64) + x_lo
 // (vector precision, the pass's running correction).  Folding moves x_lo into x_hi;
@@ -784,6 +795,14 @@ int engine_apply(const Operator &op, int precision, int T, int ntiles, const voi
                  void *stream) {
     return dispatch<ApplyLauncher>(precision, T, op.kind, op, ntiles, x, y,
                                    static_cast<cudaStream_t>(stream));
+}
+
+int engine_fill_diag(const Operator &op, double *diag_d, float *diag_f, void *stream) {
+    int blocks = (int)((op.n + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_fill_diag<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(op, diag_d, diag_f);
+    return (int)cudaGetLastError();
 }
 
 int engine_true_residual(const Solve &s, int set, int col_begin, int col_end, int replace,

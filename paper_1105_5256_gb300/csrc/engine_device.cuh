@@ -136,6 +136,24 @@ __device__ __forceinline__ float field_at<float>(const Operator &op, int64_t i) 
     return op.field_f ? op.kappa2_f * op.field_f[i] : op.kappa2_f;
 }
 
+// the 2D5/3D7 diagonal term kappa2_i + tau mask_i (without the Laplacian's degree)
+template <typename V>
+__device__ __forceinline__ V diag_at(const Operator &op, int64_t i) {
+    if constexpr (sizeof(V) == 8) {
+        if (op.diag_d) return op.diag_d[i];
+    } else {
+        if (op.diag_f) return op.diag_f[i];
+    }
+    V dg = field_at<V>(op, i);
+    if (op.mask) dg += op_tau<V>(op) * (V)op.mask[i];
+    return dg;
+}
+template <typename V>
+__device__ __forceinline__ const V *diag_ptr(const Operator &op) {
+    if constexpr (sizeof(V) == 8) return op.diag_d;
+    else return op.diag_f;
+}
+
 // Lattice neighbour of (x, y, z) shifted by (dx, dy, dz): wrapped on a torus,
 // -1 outside a Dirichlet-truncated grid.
 __device__ __forceinline__ int64_t lattice_nbr(const Operator &op, int x, int y, int z, int dx,
@@ -198,8 +216,7 @@ __device__ __forceinline__ void apply_row(const Operator &op, int64_t i, const L
                 ++nb;
             }
         }
-        V dg = field_at<V>(op, i) + (V)(NB - nb);
-        if (op.mask) dg += op_tau<V>(op) * (V)op.mask[i];
+        const V dg = diag_at<V>(op, i) + (V)(NB - nb);
         const V sc = op_scale<V>(op);
 #pragma unroll
         for (int t = 0; t < T; ++t) w[t] = sc * fma(dg, self[t], acc[t]);
@@ -689,6 +706,15 @@ __device__ __forceinline__ void cp_async_pack(Pack<V, TS> *dst, const V *src, bo
                          "l"(g + 8 * k), "r"(valid ? 8 : 0));
     }
 }
+// one 4- or 8-byte word (src-size 0 zero-fills)
+template <typename V>
+__device__ __forceinline__ void cp_async_word(V *dst, const V *src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(V) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
@@ -810,7 +836,7 @@ template <typename V, int T, int G>
 constexpr size_t stream_smem_bytes() {
     constexpr int TS = T / G;
     constexpr size_t pk = sizeof(Pack<V, TS>);
-    constexpr size_t rows = (4 + 3 * STREAM_PD) * SW * G * pk + STREAM_PD * SW * G * sizeof(int);
+    constexpr size_t rows = (4 + 3 * STREAM_PD) * SW * G * pk + STREAM_PD * SW * G * (sizeof(int) + sizeof(V));
     constexpr size_t part = (size_t)SW * G * NDOT * TS * sizeof(V);
     constexpr size_t red = (size_t)SW * G * sizeof(double);
     return rows > part ? (rows > red ? rows : red) : (part > red ? part : red);
@@ -845,6 +871,9 @@ __device__ __forceinline__ void stream_sweep(const Solve &s, int tile, int cur, 
     P *const us = ps + 2 * NT;
     P *const ring = ps + 4 * NT + threadIdx.x;
     int *const ringc = reinterpret_cast<int *>(ps + (4 + 3 * PD) * NT) + threadIdx.x;
+    // diagonal terms of field / mask models ride in the ring too (one word a vertex)
+    V *const ringd = reinterpret_cast<V *>(reinterpret_cast<int *>(ps + (4 + 3 * PD) * NT) + PD * NT) + threadIdx.x;
+    const V *const diag = KIND == KIND_2D5 ? diag_ptr<V>(s.op) : nullptr;
     const int nx = s.op.nx, ny = s.op.ny;
     const bool per = s.op.periodic;
     const int xl = threadIdx.x / G, g = threadIdx.x - xl * G;
@@ -885,6 +914,7 @@ __device__ __forceinline__ void stream_sweep(const Solve &s, int tile, int cur, 
             asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dc),
                          "l"(s.colour + (in ? (int64_t)gyw * nx + gxw : 0)), "r"(in ? 4 : 0));
         }
+        if (diag) cp_async_word<V>(ringd + slot * NT, diag + (in ? (int64_t)gyw * nx + gxw : 0), in);
         cp_async_commit();
     };
     // outputs at (gx, y) of lattice row y held in ring slot `slot`
@@ -962,9 +992,7 @@ __device__ __forceinline__ void stream_sweep(const Solve &s, int tile, int cur, 
         } else {
             // w = Q p at (x, y-1): p row y-1 was shared last step
             if (y - 1 >= ys && y - 1 < ye && outx) {
-                const int64_t gi = (int64_t)(y - 1) * nx + gx;
-                V dg = field_at<V>(s.op, gi);
-                if (s.op.mask) dg += op_tau<V>(s.op) * (V)s.op.mask[gi];
+                const V dg = diag ? ringd[slot_h * NT] : op_kappa2<V>(s.op);
                 const P *row = ps + ((y - 1) & 1) * NT;
                 const P wk = M::mul(sc, diff5p<V, TS>(M::splat(dg), pw1, row[threadIdx.x - G], row[threadIdx.x + G], pw0, pw2));
                 emit(y - 1, slot_h, pw1, wk);
@@ -1220,9 +1248,7 @@ __device__ __forceinline__ void stream_sweep_bulk(const Solve &s, int tile, int 
             }
         } else {
             if (y - 1 >= ys && y - 1 < ye && outx) {
-                const int64_t gi = (int64_t)(y - 1) * nx + gx;
-                V dg = field_at<V>(s.op, gi);
-                if (s.op.mask) dg += op_tau<V>(s.op) * (V)s.op.mask[gi];
+                const V dg = diag_at<V>(s.op, (int64_t)(y - 1) * nx + gx);
                 const P *row = ps + ((y - 1) & 1) * NT;
                 const P wk = M::mul(sc, diff5p<V, T>(M::splat(dg), pw1, row[threadIdx.x - 1], row[threadIdx.x + 1], pw0, pw2));
                 emit(y - 1, slot_h, pw1, wk);
@@ -1294,7 +1320,7 @@ constexpr int P3X = 32, P3Y = 8, P3T = P3X * P3Y;
 template <typename V, int T>
 constexpr size_t stream3d_smem_bytes() {
     constexpr size_t pk = sizeof(Pack<V, T>);
-    constexpr size_t rows = (2 + 3 * STREAM_PD) * P3T * pk + STREAM_PD * P3T * sizeof(int);
+    constexpr size_t rows = (2 + 3 * STREAM_PD) * P3T * pk + STREAM_PD * P3T * (sizeof(int) + sizeof(V));
     constexpr size_t part = (size_t)P3T * NDOT * T * sizeof(V);
     constexpr size_t red = (size_t)P3T * sizeof(double);
     return rows > part ? (rows > red ? rows : red) : (part > red ? part : red);
@@ -1314,6 +1340,8 @@ __global__ void __launch_bounds__(P3T, stream3d_min_blocks<V, T>()) k_stream3d(S
     P *const ps = reinterpret_cast<P *>(smem);                    // 2 planes
     P *const ring = ps + 2 * P3T + threadIdx.x;
     int *const ringc = reinterpret_cast<int *>(ps + (2 + 3 * PD) * P3T) + threadIdx.x;
+    V *const ringd = reinterpret_cast<V *>(reinterpret_cast<int *>(ps + (2 + 3 * PD) * P3T) + PD * P3T) + threadIdx.x;
+    const V *const diag = diag_ptr<V>(s.op);
     const int nx = s.op.nx, ny = s.op.ny, nz = s.op.nz;
     const bool per = s.op.periodic;
     const int xl = threadIdx.x % P3X, yl = threadIdx.x / P3X;
@@ -1357,6 +1385,7 @@ __global__ void __launch_bounds__(P3T, stream3d_min_blocks<V, T>()) k_stream3d(S
         const unsigned dc = (unsigned)__cvta_generic_to_shared(ringc + slot * P3T);
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dc),
                      "l"(s.colour + vtx), "r"(in ? 4 : 0));
+        if (diag) cp_async_word<V>(ringd + slot * P3T, diag + vtx, in);
         cp_async_commit();
     };
     P pw0 = zero_pack<V, T>(), pw1 = pw0, pw2 = pw0;   // p at planes z-2, z-1, z
@@ -1378,8 +1407,7 @@ __global__ void __launch_bounds__(P3T, stream3d_min_blocks<V, T>()) k_stream3d(S
         const int slot_h = slot - H < 0 ? slot - H + PD : slot - H;
         if (z - 1 >= zs && z - 1 < ze && out) {
             const int64_t gi = (int64_t)(z - 1) * plane + (int64_t)gy * nx + gx;
-            V dg = field_at<V>(s.op, gi);
-            if (s.op.mask) dg += op_tau<V>(s.op) * (V)s.op.mask[gi];
+            const V dg = diag ? ringd[slot_h * P3T] : op_kappa2<V>(s.op);
             const P *pl = ps + ((z - 1) & 1) * P3T;
             const P c = pw1;
             const P h = M::add(M::add(M::sub(c, pl[threadIdx.x - 1]), M::sub(c, pl[threadIdx.x + 1])),

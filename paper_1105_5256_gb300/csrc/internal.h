@@ -40,6 +40,10 @@ struct Operator {
     const double *field_d;   // kappa2 field base values, FP64 copy
     const float *field_f;    // FP32 copy
     const uint8_t *mask;     // observation mask (or nullptr)
+    // 2D5/3D7 with a field or a mask: the diagonal term kappa2*field_i + tau*mask_i per
+    // vertex (FP64, and rounded once to FP32), so that passes read one word per vertex
+    const double *diag_d;
+    const float *diag_f;
     const int64_t *rowptr;   // CSR
     const int32_t *colidx;
     const double *val_d;
@@ -117,6 +121,8 @@ int engine_finish(const Solve &s, int col_begin, int col_end, void *stream);
 int engine_apply(const Operator &op, int precision, int T, int ntiles, const void *x, void *y,
                  void *stream);
 int engine_grad_params(const Solve &s, int nparam, const int *ids, double *out_dev, void *stream);
+// diag_d[i] = kappa2 * (field ? field[i] : 1) + tau * (mask ? mask[i] : 0), diag_f its FP32 copy
+int engine_fill_diag(const Operator &op, double *diag_d, float *diag_f, void *stream);
 // reliable updates: x_hi += x_lo, x_lo = 0 (all tiles); then with replace != 0 the active
 // tiles' residuals in set `set` become v - Q x_hi.  norm2_dev[ncols] (zeroed here) receives
 // ||v_c - Q x_c||^2 in FP64 for c in [col_begin, col_end), x = x_hi when present, else x.

@@ -14,6 +14,8 @@ import synth
 from oracle import closed_forms as cf
 from oracle import hht
 from oracle import method as mt
+from oracle import matrices as om
+from colour_check import checked_colouring
 
 pytestmark = pytest.mark.gpu
 NSHIFT = 20
@@ -53,7 +55,7 @@ def test_small_batch_matches_single_contexts_and_oracle(prec, tol, rel):
         v, _ = L.ld_logdet(ctx)
         terms, _ = L.ld_column_terms(ctx)
         assert abs(vals[k] - v) <= 50 * tol * np.abs(terms).sum()
-        col, _ = L.ld_get_colouring(ctx)
+        col, _ = checked_colouring(ctx, om.precision(inst.kind, inst.dims, inst.kappa2), inst.distance)
         ref = target(inst, col)
         if rel is None:
             assert abs(vals[k] - ref) <= 50 * tol * np.abs(terms).sum()

@@ -21,6 +21,7 @@ from oracle import hht
 from oracle import matrices as om
 from oracle import method as mt
 from oracle import probing
+from colour_check import checked_colouring, checked_on_subbox
 
 pytestmark = pytest.mark.gpu
 
@@ -62,8 +63,8 @@ def test_posterior_128_gradients_vs_oracle_traces(prec):
     ctx = L.ld_create(L.grid_matrix(L.LD_STENCIL_2D5, dims, k2, tau=tau, obs_mask=mask), 4, 20, tol,
                       L.options(precision=prec))
     v, g, _ = L.ld_logdet_grad(ctx, [L.LD_P_KAPPA2, L.LD_P_TAU])
-    col, _ = L.ld_get_colouring(ctx)
     Q = om.precision(om.KIND_2D5, dims, k2, tau=tau, mask=mask)
+    col, _ = checked_colouring(ctx, Q, 4)
     V = probing.probing_vectors(col)
     X = sp.linalg.splu(Q.tocsc()).solve(V)
     probed_k2 = float(np.sum(V * X))
@@ -87,6 +88,7 @@ def test_3d_256_constant_field_sampled_colours():
                       L.options(precision=L.LD_MIXED))
     v, info = L.ld_logdet(ctx)
     col, nc = L.ld_get_colouring(ctx)
+    checked_on_subbox(col, dims, 6)
     terms, _ = L.ld_column_terms(ctx)
     lo, hi = mt.spectral_bounds(om.KIND_3D7, dims, k2)
     s, a = hht.log_nodes(lo, hi, 32)
@@ -108,8 +110,8 @@ def test_3d_seeded_field_exact_solves_and_gradient(prec):
     ctx = L.ld_create(L.grid_matrix(L.LD_STENCIL_3D7, dims, 1.0, kappa2_field=f), 6, 32, tol,
                       L.options(precision=prec, keep_x0=1))
     v, g, info = L.ld_logdet_grad(ctx, [L.LD_P_KAPPA2])
-    col, _ = L.ld_get_colouring(ctx)
     Q = om.precision(om.KIND_3D7, dims, f)
+    col, _ = checked_colouring(ctx, Q, 6)
     lo, hi = mt.spectral_bounds(om.KIND_3D7, dims, f)
     s, a = hht.log_nodes(lo, hi, 32)
     ref = mt.probed_rational_band(Q, col, s, a, per_colour=True)
@@ -137,8 +139,8 @@ def test_3d_streaming_engine_matches_exact_solves(dims, per):
                                     tau=2.0, obs_mask=mask), 2, 20, tol,
                       L.options(precision=L.LD_FP64, engine=1, keep_x0=1))
     v, g, info = L.ld_logdet_grad(ctx, [L.LD_P_KAPPA2, L.LD_P_TAU])
-    col, _ = L.ld_get_colouring(ctx)
     Q = om.precision(om.KIND_3D7, dims, 0.7 * f, periodic=per, tau=2.0, mask=mask)
+    col, _ = checked_colouring(ctx, Q, 2)
     lo, hi = mt.spectral_bounds(om.KIND_3D7, dims, 0.7 * f, periodic=per, tau=2.0, mask=mask)
     s, a = hht.log_nodes(lo, hi, 20)
     if per:   # wrap-around entries make the band as wide as the matrix: dense route

@@ -14,6 +14,8 @@ import synth
 from oracle import closed_forms as cf
 from oracle import hht
 from oracle import method as mt
+from oracle import matrices as om
+from colour_check import checked_colouring
 
 pytestmark = pytest.mark.gpu
 
@@ -43,7 +45,7 @@ def test_matern_1024_against_spectral_oracle(prec, tol):
     k2 = float(synth.kappa2_draws(2, 16)[1])
     ctx = L.ld_create(L.grid_matrix(KIND, DIMS, k2), DIST, NSHIFT, tol, L.options(precision=prec))
     val, info = L.ld_logdet(ctx)
-    col, nc = L.ld_get_colouring(ctx)
+    col, nc = checked_colouring(ctx, om.precision(KIND, DIMS, k2), DIST)
     assert nc == 18
     terms, _ = L.ld_column_terms(ctx)
     ref = target(k2, col)
@@ -64,6 +66,6 @@ def test_gradient_fullsize_periodic_5pt():
     dims, k2, tol = (1024, 1024), 0.05, 1e-8
     ctx = L.ld_create(L.grid_matrix(L.LD_STENCIL_2D5, dims, k2, periodic=True), 4, NSHIFT, tol)
     v, g, info = L.ld_logdet_grad(ctx, [L.LD_P_KAPPA2])
-    col, _ = L.ld_get_colouring(ctx)
+    col, _ = checked_colouring(ctx, om.precision(om.KIND_2D5, dims, k2, periodic=True), 4)
     gref = cf.probed_value(L.LD_STENCIL_2D5, dims, k2, True, col, lambda lam: 1.0 / lam)
     assert abs(g[0] - gref) <= 1e-6 * abs(gref)

@@ -20,6 +20,7 @@ from oracle import hht
 from oracle import matrices as om
 from oracle import method as mt
 from oracle import probing
+from colour_check import checked_colouring
 
 pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -65,7 +66,7 @@ def test_vector_form_cross_checks_projected_terms():
                       L.options(precision=L.LD_FP64))
     L.ld_logdet(ctx)
     terms, _ = L.ld_column_terms(ctx)
-    col, nc = L.ld_get_colouring(ctx)
+    col, nc = checked_colouring(ctx, om.precision(om.KIND_2D13_SQ, dims, k2), 2)
     Vp = probing.probing_vectors(col)
     Y, _ = L.ld_logmv(ctx, Vp)
     vec_terms = np.sum(Vp * Y, axis=0)

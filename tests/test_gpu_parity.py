@@ -21,6 +21,7 @@ from oracle import hht
 from oracle import matrices as om
 from oracle import method as mt
 from oracle import probing
+from colour_check import checked_colouring
 
 pytestmark = pytest.mark.gpu
 
@@ -142,7 +143,7 @@ def test_matern_dirichlet(prec, tol, dims, k2):
     kind = om.KIND_2D13_SQ
     ctx = L.ld_create(L.grid_matrix(kind, dims, k2), 2, 20, tol, L.options(precision=prec))
     val, info = L.ld_logdet(ctx)
-    col, _ = L.ld_get_colouring(ctx)
+    col, _ = checked_colouring(ctx, om.precision(kind, dims, k2), 2)
     lo, hi = mt.spectral_bounds(kind, dims, k2)
     s, a = hht.log_nodes(lo, hi, 20)
     target = spectral_target(kind, dims, k2, False, col, s, a, per_colour=True)
@@ -161,8 +162,8 @@ def test_3d_field_against_exact_shifted_solves(prec):
     ctx = L.ld_create(L.grid_matrix(om.KIND_3D7, dims, 1.0, kappa2_field=f), 3, 24, tol,
                       L.options(precision=prec))
     val, info = L.ld_logdet(ctx)
-    col, _ = L.ld_get_colouring(ctx)
     Q = om.precision(om.KIND_3D7, dims, f)
+    col, _ = checked_colouring(ctx, Q, 3)
     lo, hi = mt.spectral_bounds(om.KIND_3D7, dims, f)
     s, a = hht.log_nodes(lo, hi, 24)
     target = mt.probed_rational_band(Q, col, s, a, per_colour=True)
@@ -177,8 +178,8 @@ def test_masked_posterior_against_exact_shifted_solves():
     k2, tau, tol = 0.1, 4.0, 1e-10
     ctx = L.ld_create(L.grid_matrix(om.KIND_2D5, dims, k2, tau=tau, obs_mask=mask), 4, 20, tol)
     val, info = L.ld_logdet(ctx)
-    col, _ = L.ld_get_colouring(ctx)
     Q = om.precision(om.KIND_2D5, dims, k2, tau=tau, mask=mask)
+    col, _ = checked_colouring(ctx, Q, 4)
     lo, hi = mt.spectral_bounds(om.KIND_2D5, dims, k2, tau=tau, mask=mask)
     s, a = hht.log_nodes(lo, hi, 20)
     target = mt.probed_rational_band(Q, col, s, a, per_colour=True)
@@ -249,7 +250,7 @@ def test_gradient_kappa2_projected_and_stored_agree():
     ctx2 = L.ld_create(L.grid_matrix(om.KIND_2D5, dims, k2), 4, 20, tol, L.options(keep_x0=1))
     v2, _ = L.ld_logdet(ctx2)
     g2 = L.ld_grad(ctx2, [L.LD_P_KAPPA2, L.LD_P_SCALE])
-    col, _ = L.ld_get_colouring(ctx)
+    col, _ = checked_colouring(ctx, om.precision(om.KIND_2D5, dims, k2), 4)
     ref = cf.probed_value(om.KIND_2D5, dims, k2, False, col, lambda x: 1 / x)
     assert abs(g1[0] - ref) <= 1e-8 * abs(ref)
     assert abs(g2[0] - ref) <= 1e-8 * abs(ref)
@@ -262,7 +263,7 @@ def test_gradient_matern_and_mask_against_oracle():
     tol = 1e-10
     ctx = L.ld_create(L.grid_matrix(om.KIND_2D13_SQ, dims, k2, scale=2.0), 2, 20, tol)
     _, g, _ = L.ld_logdet_grad(ctx, [L.LD_P_KAPPA2, L.LD_P_SCALE])
-    col, _ = L.ld_get_colouring(ctx)
+    col, _ = checked_colouring(ctx, om.precision(om.KIND_2D13_SQ, dims, k2), 2)
     # dQ/dkappa2 = 2 s Q1 shares Q's eigenvectors: probed sum 2 s lambda1 / (s lambda1^2)
     lam1 = lambda lam: np.sqrt(lam / 2.0)
     ref = cf.probed_value(om.KIND_2D13_SQ, dims, k2, False, col, lambda lam: 2.0 * 2.0 * lam1(lam) / lam,
@@ -275,8 +276,8 @@ def test_gradient_matern_and_mask_against_oracle():
     mask = synth.obs_mask(4, n2, 0.1)
     ctx2 = L.ld_create(L.grid_matrix(om.KIND_2D5, dims2, 0.1, tau=4.0, obs_mask=mask), 4, 20, tol)
     _, g2, _ = L.ld_logdet_grad(ctx2, [L.LD_P_KAPPA2, L.LD_P_TAU])
-    col2, _ = L.ld_get_colouring(ctx2)
     Q2 = om.precision(om.KIND_2D5, dims2, 0.1, tau=4.0, mask=mask)
+    col2, _ = checked_colouring(ctx2, Q2, 4)
     V = probing.probing_vectors(col2)
     X = np.linalg.solve(Q2.toarray(), V)
     ref_k2 = float(np.sum(V * X))
