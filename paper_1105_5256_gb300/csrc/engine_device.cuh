@@ -1316,22 +1316,25 @@ __global__ void __launch_bounds__(SW * G, stream_min_blocks_t<V, T>()) k_stream2
 // thread's register window.  Out-of-grid entries are zero (Dirichlet ghosts of the
 // difference form); a torus wraps.
 constexpr int P3X = 32, P3Y = 8, P3T = P3X * P3Y;
+// plane ring depth: a plane step moves 256 lattice columns, so two planes in flight
+// suffice, and the smaller ring lets three CTAs share an SM for packs up to 16 bytes
+constexpr int P3_PD = 4;
 
 template <typename V, int T>
 constexpr size_t stream3d_smem_bytes() {
     constexpr size_t pk = sizeof(Pack<V, T>);
-    constexpr size_t rows = (2 + 3 * STREAM_PD) * P3T * pk + STREAM_PD * P3T * (sizeof(int) + sizeof(V));
+    constexpr size_t rows = (2 + 3 * P3_PD) * P3T * pk + P3_PD * P3T * (sizeof(int) + sizeof(V));
     constexpr size_t part = (size_t)P3T * NDOT * T * sizeof(V);
     constexpr size_t red = (size_t)P3T * sizeof(double);
     return rows > part ? (rows > red ? rows : red) : (part > red ? part : red);
 }
 
 template <typename V, int T>
-__host__ __device__ constexpr int stream3d_min_blocks() { return sizeof(V) * T <= 8 ? 3 : 2; }
+__host__ __device__ constexpr int stream3d_min_blocks() { return sizeof(V) * T <= 16 ? 3 : 2; }
 
 template <typename V, int T, bool KEEPX>
 __global__ void __launch_bounds__(P3T, stream3d_min_blocks<V, T>()) k_stream3d(Solve s, int cur) {
-    constexpr int K = NDOT * T, PD = STREAM_PD, H = 1;
+    constexpr int K = NDOT * T, PD = P3_PD, H = 1;
     using P = Pack<V, T>;
     using M = PackMath<V, T>;
     const int tile = launch_tile(s);
