@@ -828,15 +828,18 @@ __device__ __forceinline__ Pack<V, TS> diff5(V c, const Pack<V, TS> &pc, const P
 // resident CTAs per SM the register budget is sized for
 constexpr int stream_min_blocks(int G) { return G == 1 ? 3 : 2; }
 template <typename V, int T>
-__host__ __device__ constexpr int stream_min_blocks_t() { return sizeof(V) * T <= 8 ? 6 : (sizeof(V) * T <= 16 ? 4 : 3); }
+__host__ __device__ constexpr int stream_min_blocks_t() { return sizeof(V) * T <= 8 ? 6 : (sizeof(V) * T <= 16 ? 5 : 3); }
 
 constexpr int STREAM_PD = 6;   // ring depth: rows held per thread (cp.async)
 
-template <typename V, int T, int G>
+// dynamic shared memory of a streaming sweep; the ring of diagonal terms only for the
+// 5-point kind (KIND_2D5; the batched kernel, which runs both kinds, passes it too)
+template <typename V, int T, int G, int KIND = KIND_2D5>
 constexpr size_t stream_smem_bytes() {
     constexpr int TS = T / G;
     constexpr size_t pk = sizeof(Pack<V, TS>);
-    constexpr size_t rows = (4 + 3 * STREAM_PD) * SW * G * pk + STREAM_PD * SW * G * (sizeof(int) + sizeof(V));
+    constexpr size_t dg = KIND == KIND_2D5 ? sizeof(V) : 0;
+    constexpr size_t rows = (4 + 3 * STREAM_PD) * SW * G * pk + STREAM_PD * SW * G * (sizeof(int) + dg);
     constexpr size_t part = (size_t)SW * G * NDOT * TS * sizeof(V);
     constexpr size_t red = (size_t)SW * G * sizeof(double);
     return rows > part ? (rows > red ? rows : red) : (part > red ? part : red);

@@ -14,7 +14,7 @@ struct IterLauncher {
         dim3 grid(s.bpt, nt);
         if constexpr (KIND == KIND_2D5 || KIND == KIND_2D13_SQ) {
             constexpr int G = stream_groups<V, T>();
-            constexpr size_t sm = stream_smem_bytes<V, T, G>(), smb = stream_bulk_smem_bytes<V, T>();
+            constexpr size_t sm = stream_smem_bytes<V, T, G, KIND>(), smb = stream_bulk_smem_bytes<V, T>();
             if (s.bulk) {
                 if (s.keep_x0)
                     k_stream2d<V, T, 1, KIND, true, true><<<grid, SW, smb, st>>>(s, cur);
@@ -44,7 +44,7 @@ struct OccLauncher {
         int a = 0, b = 0;
         if constexpr (KIND == KIND_2D5 || KIND == KIND_2D13_SQ) {
             constexpr int G = stream_groups<V, T>();
-            constexpr size_t sm = stream_smem_bytes<V, T, G>(), smb = stream_bulk_smem_bytes<V, T>();
+            constexpr size_t sm = stream_smem_bytes<V, T, G, KIND>(), smb = stream_bulk_smem_bytes<V, T>();
             if (cudaFuncSetAttribute(k_stream2d<V, T, G, KIND, false, false>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
                 cudaFuncSetAttribute(k_stream2d<V, T, G, KIND, true, false>,
