@@ -107,3 +107,19 @@ def circulant_probed_log(dims, kappa2, colour: np.ndarray) -> float:
         auto = np.real(sfft.ifftn(V * np.conj(V)))
         total += float(np.sum(ell * auto))
     return total
+
+
+def log_column(kind, dims, kappa2, periodic, j: int, scale=1.0) -> np.ndarray:
+    """y = log(Q) e_j exactly, by the eigenbasis: y = U diag(log lambda) U^T e_j with U
+    the orthonormal DST-I (Dirichlet) or DFT (periodic) basis of the grid."""
+    dims = [int(d) for d in dims]
+    shape = tuple(reversed(dims))
+    lam = eig_grid(kind, dims, kappa2, periodic, scale)
+    e = np.zeros(int(np.prod(dims)))
+    e[j] = 1.0
+    e = e.reshape(shape)
+    if periodic:
+        y = sfft.ifftn(np.log(lam) * sfft.fftn(e, norm="ortho"), norm="ortho").real
+    else:
+        y = sfft.idstn(np.log(lam) * sfft.dstn(e, type=1, norm="ortho"), type=1, norm="ortho")
+    return y.reshape(-1)

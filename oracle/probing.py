@@ -56,3 +56,49 @@ def probing_vectors(colour: np.ndarray) -> np.ndarray:
     V = np.zeros((colour.size, C))
     V[np.arange(colour.size), colour] = 1.0
     return V
+
+
+# ---------------------------------------------------------------- distance selection
+# Sec. 2.1 (heuristic for the power p of Q^p whose graph the colouring follows):
+# solve for a column x = Q^{-1} e_j, or here y = log(Q) e_j, and take
+#     p = min { d(l, j) : |y_l| < eps },
+# d the graph distance in the graph of Q.  Reading: eps is relative to |y_j| (the
+# paper's eps is unnormalised; relative makes p independent of the scale of Q).
+
+def graph_distances(Q: sp.csr_matrix, j: int, max_d: int) -> np.ndarray:
+    """Breadth-first graph distances from vertex j over the pattern of Q (int64;
+    -1 beyond max_d)."""
+    Q = Q.tocsr()
+    n = Q.shape[0]
+    dist = np.full(n, -1, dtype=np.int64)
+    dist[j] = 0
+    frontier = [int(j)]
+    for d in range(1, max_d + 1):
+        nxt = []
+        for u in frontier:
+            for w in Q.indices[Q.indptr[u]:Q.indptr[u + 1]]:
+                if dist[w] < 0:
+                    dist[w] = d
+                    nxt.append(int(w))
+        frontier = nxt
+        if not frontier:
+            break
+    return dist
+
+
+def decay_profile(y: np.ndarray, dist: np.ndarray, j: int, max_d: int) -> np.ndarray:
+    """profile[d] = max over vertices at graph distance d of |y_l| / |y_j|."""
+    y = np.abs(np.asarray(y)) / abs(y[j])
+    prof = np.zeros(max_d + 1)
+    for d in range(max_d + 1):
+        sel = dist == d
+        prof[d] = y[sel].max() if np.any(sel) else 0.0
+    return prof
+
+
+def decay_distance(y: np.ndarray, dist: np.ndarray, j: int, eps: float) -> int:
+    """min { d(l, j) : |y_l| < eps |y_j| } over vertices within the distances given
+    (-1 when none qualifies)."""
+    ratio = np.abs(np.asarray(y)) / abs(y[j])
+    sel = (dist >= 0) & (ratio < eps)
+    return int(dist[sel].min()) if np.any(sel) else -1

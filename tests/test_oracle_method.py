@@ -214,3 +214,44 @@ def test_banded_shifted_solves_equal_dense_rational_target():
     band = mt.probed_rational_band(Q, col, sigma, alpha)
     dense = mt.probed_dense(Q, col, lambda lam: hht.f_N(lam, sigma, alpha))
     assert abs(band - dense) <= 1e-11 * abs(dense)
+
+
+# ---------------------------------------------------------------- distance selection
+@pytest.mark.parametrize("kind,dims,per", [(om.KIND_2D5, (12, 10), False), (om.KIND_2D5, (9, 8), True),
+                                          (om.KIND_2D13_SQ, (11, 9), False)])
+def test_log_column_matches_dense_logm(kind, dims, per):
+    Q = om.precision(kind, dims, 0.3, periodic=per)
+    L = sla.logm(Q.toarray()).real
+    for j in (0, 17, Q.shape[0] - 1):
+        assert np.abs(cf.log_column(kind, dims, 0.3, per, j) - L[:, j]).max() <= 1e-12
+
+
+@pytest.mark.parametrize("kind,dims,per", [(om.KIND_2D5, (13, 11), False), (om.KIND_2D5, (10, 9), True),
+                                          (om.KIND_2D13_SQ, (12, 10), False), (om.KIND_3D7, (6, 5, 4), False)])
+def test_graph_distances_are_lattice_distances(kind, dims, per):
+    """Graph distance on the lattice = (torus) L1 distance for 5/7 points, ceil(L1/2) for
+    the 13-point square."""
+    Q = om.precision(kind, dims, 0.3, periodic=per)
+    j = Q.shape[0] // 2 + 1
+    dist = probing.graph_distances(Q, j, 50)
+    coords = np.array(np.unravel_index(np.arange(Q.shape[0]), tuple(reversed(dims)))).T
+    cj = coords[j]
+    diff = np.abs(coords - cj)
+    if per:
+        diff = np.minimum(diff, np.array(tuple(reversed(dims))) - diff)
+    l1 = diff.sum(axis=1)
+    ref = (l1 + 1) // 2 if kind == om.KIND_2D13_SQ else l1
+    assert np.array_equal(dist, ref)
+
+
+def test_decay_distance_definition_on_a_path():
+    """Path graph: y_l = 10^-|l-j|; the first vertex below eps sits at distance ceil(-log10 eps)."""
+    n, j = 30, 12
+    Q = path_graph(n)
+    dist = probing.graph_distances(Q, j, n)
+    y = 10.0 ** (-np.abs(np.arange(n) - j))
+    for eps, p in ((0.5, 1), (1e-3 * 1.5, 3), (1e-6 * 0.99, 7)):
+        assert probing.decay_distance(y, dist, j, eps) == p
+    prof = probing.decay_profile(y, dist, j, 5)
+    assert np.allclose(prof, 10.0 ** -np.arange(6))
+    assert probing.decay_distance(y, dist, j, 1e-40) == -1
