@@ -200,6 +200,17 @@ ld_status ld_apply(ld_ctx *ctx, int ncols, const double *x, double *y);
  * device memory for the call.  Errors as ld_logdet. */
 ld_status ld_logmv(ld_ctx *ctx, int ncols, const double *V, double *Y, ld_info *info);
 
+/* Colouring distance by decay (Sec. 2.1, the heuristic for the power p of Q^p): forms
+ * y = log(Q) e_j with the context's method (as ld_logmv: the context's operator, nodes,
+ * tolerance and precision) and returns *distance = min { d(l, j) : |y_l| < eps |y_j| },
+ * d the graph distance in the graph of Q (lattice distance for grid kinds, breadth-first
+ * search for CSR), or -1 when no vertex within max_d qualifies.  eps is relative to
+ * |y_j|.  profile: NULL or max_d + 1 doubles, profile[d] = max over vertices at graph
+ * distance d of |y_l| / |y_j|.  0 <= j < n, eps > 0, 0 <= max_d <= 4096; errors as
+ * ld_logmv. */
+ld_status ld_select_distance(ld_ctx *ctx, int64_t j, double eps, int max_d, int32_t *distance,
+                             double *profile, ld_info *info);
+
 /* Host utilities (no device work; usable without a GPU). */
 
 /* Greedy distance-d colouring of the CSR pattern in natural order (Sec. 2.1).

@@ -95,6 +95,7 @@ def library(build_if_missing: bool = False):
         "ld_get_nodes": ([vp, vp, vp, P(i32)], st),
         "ld_apply": ([vp, C.c_int, vp, vp], st),
         "ld_logmv": ([vp, C.c_int, vp, vp, P(Info)], st),
+        "ld_select_distance": ([vp, i64, dbl, C.c_int, P(i32), vp, P(Info)], st),
         "ld_colour_csr": ([i64, vp, vp, C.c_int, vp, P(i32)], st),
         "ld_colour_grid": ([C.c_int, vp, C.c_int, C.c_int, vp, P(i32)], st),
         "ld_hht_nodes": ([dbl, dbl, C.c_int, vp, vp, P(dbl)], st),
@@ -290,6 +291,17 @@ def ld_logmv(ctx: Context, V: np.ndarray):
     info = Info()
     _check(library().ld_logmv(ctx.handle, V.shape[1], _ptr(V), _ptr(Y), C.byref(info)))
     return Y, info.as_dict()
+
+
+def ld_select_distance(ctx: Context, j: int, eps: float, max_d: int = 32):
+    """Colouring distance by decay of log(Q) e_j (Sec. 2.1): returns (distance, profile,
+    info); distance -1 when no vertex within max_d falls below eps |y_j|."""
+    d = C.c_int32()
+    prof = np.zeros(int(max_d) + 1)
+    info = Info()
+    _check(library().ld_select_distance(ctx.handle, int(j), float(eps), int(max_d), C.byref(d),
+                                        _ptr(prof), C.byref(info)))
+    return int(d.value), prof, info.as_dict()
 
 
 def ld_colour_csr(rowptr, colidx, d: int):

@@ -1124,6 +1124,43 @@ ld_status ld_logmv(ld_ctx *c, int ncols, const double *V, double *Y, ld_info *in
     return LD_OK;
 }
 
+ld_status ld_select_distance(ld_ctx *c, int64_t j, double eps, int max_d, int32_t *distance,
+                             double *profile, ld_info *info) {
+    if (!c || !distance) return fail(LD_EINVAL, "bad arguments");
+    if (c->is_batch) return fail(LD_EINVAL, "batched context");
+    if (j < 0 || j >= c->n) return fail(LD_EINVAL, "vertex %lld out of range", (long long)j);
+    if (!(eps > 0.0) || !std::isfinite(eps)) return fail(LD_EINVAL, "eps must be > 0");
+    if (max_d < 0 || max_d > 4096) return fail(LD_EINVAL, "max_d must be in [0, 4096]");
+    std::vector<double> e((size_t)c->n, 0.0), y((size_t)c->n, 0.0);
+    e[(size_t)j] = 1.0;
+    if (ld_status st = ld_logmv(c, 1, e.data(), y.data(), info)) return st;
+    std::vector<int32_t> dist((size_t)c->n);
+    std::vector<int64_t> rowptr;
+    std::vector<int32_t> colidx;
+    if (c->kind == LD_CSR) {   // the pattern lives on the device only
+        rowptr.resize((size_t)c->n + 1);
+        CUDA_TRY(cudaMemcpy(rowptr.data(), c->d_rowptr.p, rowptr.size() * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        colidx.resize((size_t)std::max<int64_t>(rowptr.back(), 1));
+        CUDA_TRY(cudaMemcpy(colidx.data(), c->d_colidx.p, (size_t)rowptr.back() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    }
+    ld::graph_distances(c->kind, c->dims, c->periodic, c->n, rowptr.data(), colidx.data(), j, max_d,
+                        dist.data());
+    const double yj = std::fabs(y[(size_t)j]);
+    if (!(yj > 0.0)) return fail(LD_ENUMERIC, "log(Q) e_j has a zero diagonal entry");
+    std::vector<double> prof((size_t)max_d + 1, 0.0);
+    int best = -1;
+    for (int64_t l = 0; l < c->n; ++l) {
+        const int d = dist[(size_t)l];
+        if (d < 0) continue;
+        const double r = std::fabs(y[(size_t)l]) / yj;
+        prof[(size_t)d] = std::max(prof[(size_t)d], r);
+        if (r < eps && (best < 0 || d < best)) best = d;
+    }
+    *distance = best;
+    if (profile) std::copy(prof.begin(), prof.end(), profile);
+    return LD_OK;
+}
+
 ld_status ld_colour_csr(int64_t n, const int64_t *rowptr, const int32_t *colidx, int d,
                         int32_t *colour, int32_t *n_colours) {
     if (n < 1 || !rowptr || !colidx || !colour || d < 0) return fail(LD_EINVAL, "bad arguments");

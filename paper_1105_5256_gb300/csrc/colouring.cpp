@@ -103,4 +103,43 @@ int colour_grid(int kind, const int32_t dims[3], int periodic, int d, int32_t *c
     return ncol;
 }
 
+// Graph distances from vertex j in the graph of Q, -1 beyond max_d.  Grid kinds use
+// the lattice distance (as for the colouring); CSR a breadth-first search.
+void graph_distances(int kind, const int32_t dims[3], int periodic, int64_t n, const int64_t *rowptr,
+                     const int32_t *colidx, int64_t j, int max_d, int32_t *dist) {
+    for (int64_t i = 0; i < n; ++i) dist[i] = -1;
+    if (kind == KIND_CSR) {
+        std::vector<int64_t> frontier(1, j), next;
+        dist[j] = 0;
+        for (int d = 1; d <= max_d && !frontier.empty(); ++d) {
+            next.clear();
+            for (int64_t u : frontier)
+                for (int64_t e = rowptr[u]; e < rowptr[u + 1]; ++e) {
+                    const int64_t w = colidx[e];
+                    if (dist[w] < 0) {
+                        dist[w] = d;
+                        next.push_back(w);
+                    }
+                }
+            frontier.swap(next);
+        }
+        return;
+    }
+    const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
+    const int64_t jx = j % nx, jy = (j / nx) % ny, jz = j / (nx * ny);
+    auto axis = [&](int64_t a, int64_t b, int64_t len) {
+        int64_t dd = a > b ? a - b : b - a;
+        if (periodic && len - dd < dd) dd = len - dd;
+        return dd;
+    };
+    int64_t i = 0;
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x, ++i) {
+                int64_t l1 = axis(x, jx, nx) + axis(y, jy, ny) + axis(z, jz, nz);
+                const int64_t d = kind == KIND_2D13_SQ ? (l1 + 1) / 2 : l1;
+                if (d <= max_d) dist[i] = (int32_t)d;
+            }
+}
+
 }  // namespace ld

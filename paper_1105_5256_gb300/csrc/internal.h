@@ -131,4 +131,8 @@ int engine_true_residual(const Solve &s, int set, int col_begin, int col_end, in
 int engine_plan(Solve &s);   // sets bpt (and strips/seg); returns bpt
 const char *engine_error_string(int cuda_err);
 
+// host: graph distances from vertex j (colouring.cpp)
+void graph_distances(int kind, const int32_t dims[3], int periodic, int64_t n, const int64_t *rowptr,
+                     const int32_t *colidx, int64_t j, int max_d, int32_t *dist);
+
 }  // namespace ld
