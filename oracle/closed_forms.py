@@ -123,3 +123,13 @@ def log_column(kind, dims, kappa2, periodic, j: int, scale=1.0) -> np.ndarray:
     else:
         y = sfft.idstn(np.log(lam) * sfft.dstn(e, type=1, norm="ortho"), type=1, norm="ortho")
     return y.reshape(-1)
+
+
+def quadratic_forms(kind, dims, kappa2, periodic, Z: np.ndarray, f=np.log, scale=1.0) -> np.ndarray:
+    """z_k^T f(Q) z_k for each column z_k of Z (n x s): sum_i f(lambda_i) |u_i^T z_k|^2."""
+    dims = [int(d) for d in dims]
+    shape = tuple(reversed(dims))
+    flam = f(eig_grid(kind, dims, kappa2, periodic, scale))
+    Z = np.asarray(Z)
+    return np.array([float(np.sum(flam * spectral_coeffs(Z[:, k].reshape(shape), periodic)))
+                     for k in range(Z.shape[1])])

@@ -125,6 +125,13 @@ def random_probe_block(seed: int, n: int, c: int, dtype=np.float64) -> np.ndarra
     return g.standard_normal((n, c)).astype(dtype)
 
 
+def rademacher_block(seed: int, n: int, s: int) -> np.ndarray:
+    """n x s block of independent +-1 entries, each sign with probability 1/2 (the
+    random vectors of the Hutchinson estimator, drawn here and passed in)."""
+    g = rng(seed)
+    return np.where(g.random((n, s)) < 0.5, -1.0, 1.0)
+
+
 def random_sparse_spd_pattern(seed: int, n: int, avg_deg: int = 6):
     """Seeded irregular symmetric graph for general-CSR inputs.
 

@@ -255,3 +255,24 @@ def test_decay_distance_definition_on_a_path():
     prof = probing.decay_profile(y, dist, j, 5)
     assert np.allclose(prof, 10.0 ** -np.arange(6))
     assert probing.decay_distance(y, dist, j, 1e-40) == -1
+
+
+
+# ---------------------------------------------------------------- Hutchinson (Eq. "eq_est_eq")
+def test_quadratic_forms_match_dense_logm():
+    import synth
+    for kind, dims, per in ((om.KIND_2D5, (11, 9), True), (om.KIND_2D13_SQ, (10, 8), False)):
+        Q = om.precision(kind, dims, 0.4, periodic=per)
+        Z = synth.rademacher_block(3, Q.shape[0], 5)
+        ref = np.einsum("ik,ij,jk->k", Z, sla.logm(Q.toarray()).real, Z)
+        assert np.abs(cf.quadratic_forms(kind, dims, 0.4, per, Z) - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_hutchinson_is_unbiased_on_average():
+    """E[z^T log(Q) z] = tr log Q for Rademacher z: the mean over many draws approaches it."""
+    import synth
+    dims = (16, 16)
+    Z = synth.rademacher_block(4, 256, 4000)
+    q = cf.quadratic_forms(om.KIND_2D5, dims, 0.5, True, Z)
+    exact = cf.logdet(om.KIND_2D5, dims, 0.5, True)
+    assert abs(q.mean() - exact) <= 4 * q.std() / np.sqrt(q.size)
