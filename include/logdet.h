@@ -211,6 +211,22 @@ ld_status ld_logmv(ld_ctx *ctx, int ncols, const double *V, double *Y, ld_info *
 ld_status ld_select_distance(ld_ctx *ctx, int64_t j, double eps, int max_d, int32_t *distance,
                              double *profile, ld_info *info);
 
+/* Hutchinson estimator (Sec. 2.1, Eq. "eq_est_eq"), the stochastic alternative the
+ * probing method is compared with: tr log Q ~ (1/s) sum_k z_k^T log(Q) z_k for the s
+ * columns of Z (n x s, row-major, FP64; the caller draws them, normally +-1 with
+ * probability 1/2 each).  log(Q) Z is formed as by ld_logmv.  *estimate = the mean,
+ * *std_error = sample standard deviation / sqrt(s) (0 when s = 1), samples: NULL or s
+ * doubles z_k^T log(Q) z_k.  Errors as ld_logmv. */
+ld_status ld_hutchinson(ld_ctx *ctx, int s, const double *Z, double *estimate, double *std_error,
+                        double *samples, ld_info *info);
+
+/* Failure-path self-test of the library's bounded device waits (the paper has no
+ * counterpart): one CTA on the current device waits on a barrier that nothing
+ * completes, gives up after limit_ns nanoseconds (1e3 .. 1e10) and the call returns
+ * LD_ETIMEOUT, as a pass whose bulk copies never arrived would; LD_OK would mean the
+ * wait was not bounded as documented.  Allocates 4 bytes of device memory. */
+ld_status ld_wait_selftest(int64_t limit_ns);
+
 /* Host utilities (no device work; usable without a GPU). */
 
 /* Greedy distance-d colouring of the CSR pattern in natural order (Sec. 2.1).

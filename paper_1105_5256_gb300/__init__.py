@@ -96,6 +96,8 @@ def library(build_if_missing: bool = False):
         "ld_apply": ([vp, C.c_int, vp, vp], st),
         "ld_logmv": ([vp, C.c_int, vp, vp, P(Info)], st),
         "ld_select_distance": ([vp, i64, dbl, C.c_int, P(i32), vp, P(Info)], st),
+        "ld_hutchinson": ([vp, C.c_int, vp, P(dbl), P(dbl), vp, P(Info)], st),
+        "ld_wait_selftest": ([i64], st),
         "ld_colour_csr": ([i64, vp, vp, C.c_int, vp, P(i32)], st),
         "ld_colour_grid": ([C.c_int, vp, C.c_int, C.c_int, vp, P(i32)], st),
         "ld_hht_nodes": ([dbl, dbl, C.c_int, vp, vp, P(dbl)], st),
@@ -291,6 +293,26 @@ def ld_logmv(ctx: Context, V: np.ndarray):
     info = Info()
     _check(library().ld_logmv(ctx.handle, V.shape[1], _ptr(V), _ptr(Y), C.byref(info)))
     return Y, info.as_dict()
+
+
+def ld_wait_selftest(limit_ns: int):
+    """Bounded-wait self-test: raises LogDetError(LD_ETIMEOUT) when the device wait gave
+    up after limit_ns as documented."""
+    _check(library().ld_wait_selftest(int(limit_ns)))
+
+
+def ld_hutchinson(ctx: Context, Z: np.ndarray):
+    """Hutchinson estimate of tr log Q from the columns of Z (n x s): returns
+    (estimate, standard error, per-column samples, info)."""
+    Z = np.ascontiguousarray(Z, dtype=np.float64)
+    if Z.ndim == 1:
+        Z = Z[:, None]
+    est, se = C.c_double(), C.c_double()
+    q = np.zeros(Z.shape[1])
+    info = Info()
+    _check(library().ld_hutchinson(ctx.handle, Z.shape[1], _ptr(Z), C.byref(est), C.byref(se),
+                                   _ptr(q), C.byref(info)))
+    return est.value, se.value, q, info.as_dict()
 
 
 def ld_select_distance(ctx: Context, j: int, eps: float, max_d: int = 32):

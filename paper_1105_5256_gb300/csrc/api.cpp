@@ -1124,6 +1124,39 @@ ld_status ld_logmv(ld_ctx *c, int ncols, const double *V, double *Y, ld_info *in
     return LD_OK;
 }
 
+ld_status ld_wait_selftest(int64_t limit_ns) {
+    if (limit_ns < 1000 || limit_ns > 10000000000LL) return fail(LD_EINVAL, "limit_ns out of range");
+    DevBuf st;
+    CUDA_TRY(st.alloc(sizeof(int32_t)));
+    CUDA_TRY(cudaMemset(st.p, 0xff, sizeof(int32_t)));
+    ENGINE_TRY(ld::engine_wait_selftest((uint64_t)limit_ns, st.as<int32_t>(), nullptr));
+    int32_t h = -1;
+    CUDA_TRY(cudaMemcpy(&h, st.p, sizeof h, cudaMemcpyDeviceToHost));
+    if (h == ld::DEV_TIMEOUT) return fail(LD_ETIMEOUT, "device wait gave up after %lld ns", (long long)limit_ns);
+    if (h == ld::DEV_OK) return LD_OK;
+    return fail(LD_ECUDA, "self-test kernel did not report (status %d)", h);
+}
+
+ld_status ld_hutchinson(ld_ctx *c, int s, const double *Z, double *estimate, double *std_error,
+                        double *samples, ld_info *info) {
+    if (!c || !Z || !estimate || s < 1) return fail(LD_EINVAL, "bad arguments");
+    if (c->is_batch) return fail(LD_EINVAL, "batched context");
+    std::vector<double> Y((size_t)c->n * s);
+    if (ld_status st = ld_logmv(c, s, Z, Y.data(), info)) return st;
+    std::vector<double> q((size_t)s, 0.0);
+    for (int64_t i = 0; i < c->n; ++i)
+        for (int k = 0; k < s; ++k) q[(size_t)k] += Z[(size_t)i * s + k] * Y[(size_t)i * s + k];
+    double mean = 0.0;
+    for (double v : q) mean += v;
+    mean /= s;
+    double var = 0.0;
+    for (double v : q) var += (v - mean) * (v - mean);
+    *estimate = mean;
+    if (std_error) *std_error = s > 1 ? std::sqrt(var / (s - 1) / s) : 0.0;
+    if (samples) std::copy(q.begin(), q.end(), samples);
+    return LD_OK;
+}
+
 ld_status ld_select_distance(ld_ctx *c, int64_t j, double eps, int max_d, int32_t *distance,
                              double *profile, ld_info *info) {
     if (!c || !distance) return fail(LD_EINVAL, "bad arguments");

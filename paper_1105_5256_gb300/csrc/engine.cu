@@ -435,6 +435,22 @@ __global__ void k_apply(Operator op, int ntiles, const V *x, V *y) {
     }
 }
 
+// ------------------------------------------------------------------ bounded-wait self-test
+// One CTA waits on an mbarrier that nothing arrives at: the bounded wait must give up
+// after limit_ns and report DEV_TIMEOUT through the status word, leaving the context
+// usable (the failure path of the bulk-copy waits, exercised without a fault).
+__global__ void k_wait_selftest(uint64_t limit_ns, int32_t *status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0u, limit_ns);
+    __syncthreads();
+    if (threadIdx.x == 0) *status = ok ? DEV_OK : DEV_TIMEOUT;
+}
+
 // ------------------------------------------------------------------ diagonal coefficients
 __global__ void k_fill_diag(Operator op, double *dd, float *df) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < op.n;
@@ -795,6 +811,11 @@ int engine_apply(const Operator &op, int precision, int T, int ntiles, const voi
                  void *stream) {
     return dispatch<ApplyLauncher>(precision, T, op.kind, op, ntiles, x, y,
                                    static_cast<cudaStream_t>(stream));
+}
+
+int engine_wait_selftest(uint64_t limit_ns, int32_t *status_dev, void *stream) {
+    k_wait_selftest<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(limit_ns, status_dev);
+    return (int)cudaGetLastError();
 }
 
 int engine_fill_diag(const Operator &op, double *diag_d, float *diag_f, void *stream) {

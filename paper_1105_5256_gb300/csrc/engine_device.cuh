@@ -1045,8 +1045,9 @@ __device__ __forceinline__ uint64_t global_ns() {
     asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
     return t;
 }
-// wait for phase `parity` of the barrier; gives up after about a second (false)
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+// wait for phase `parity` of the barrier; gives up after limit_ns (false)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity,
+                                          uint64_t limit_ns = 1000000000ull) {
     const unsigned a = smem_u32(bar);
     uint64_t t0 = 0;
     for (unsigned it = 0;; ++it) {
@@ -1061,7 +1062,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
         if ((it & 63) == 0) {
             const uint64_t t = global_ns();
             if (it == 0) t0 = t;
-            else if (t - t0 > 1000000000ull) return false;
+            else if (t - t0 > limit_ns) return false;
         }
     }
 }

@@ -121,6 +121,9 @@ int engine_finish(const Solve &s, int col_begin, int col_end, void *stream);
 int engine_apply(const Operator &op, int precision, int T, int ntiles, const void *x, void *y,
                  void *stream);
 int engine_grad_params(const Solve &s, int nparam, const int *ids, double *out_dev, void *stream);
+// one CTA waits on an mbarrier nothing arrives at, giving up after limit_ns: writes
+// DEV_TIMEOUT (or DEV_OK) to *status_dev
+int engine_wait_selftest(uint64_t limit_ns, int32_t *status_dev, void *stream);
 // diag_d[i] = kappa2 * (field ? field[i] : 1) + tau * (mask ? mask[i] : 0), diag_f its FP32 copy
 int engine_fill_diag(const Operator &op, double *diag_d, float *diag_f, void *stream);
 // reliable updates: x_hi += x_lo, x_lo = 0 (all tiles); then with replace != 0 the active

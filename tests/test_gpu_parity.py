@@ -316,3 +316,23 @@ def test_autograd_backward_runs_native_gradient():
     assert abs(k2.grad.item() - 3 * g[0]) <= 1e-10 * abs(g[0])
     assert abs(tau.grad.item() - 3 * g[1]) <= 1e-10 * abs(g[1])
     assert abs(sc.grad.item() - 3 * 1024) <= 1e-6 * 1024
+
+
+def test_bounded_device_wait_reports_timeout_and_context_stays_usable():
+    """A device wait that nothing completes gives up after its limit and the host reads
+    LD_ETIMEOUT; the device then runs an ordinary evaluation (failure path of the
+    bulk-copy waits, tested without a fault)."""
+    import time
+    t0 = time.perf_counter()
+    with pytest.raises(L.LogDetError) as e:
+        L.ld_wait_selftest(50_000_000)          # 50 ms
+    assert e.value.status == L.LD_ETIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    dims = (32, 32)
+    Q = om.precision(om.KIND_2D5, dims, 0.5, periodic=True)
+    col = probing.colour_greedy(Q, 2)
+    ctx = L.ld_create(L.grid_matrix(om.KIND_2D5, dims, 0.5, periodic=True), 2, 24, 1e-10,
+                      L.options(colouring=col))
+    v, _ = L.ld_logdet(ctx)
+    ref = cf.probed_value(om.KIND_2D5, dims, 0.5, True, col, np.log)
+    assert abs(v - ref) <= 1e-7 * abs(ref)
