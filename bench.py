@@ -196,6 +196,78 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_small_configs(args):
+    """The other two configurations, one JSON line each:
+    periodic64: Q = 0.5 I - Lap on a 64 x 64 torus (5-point), distance 4, N = 20, tol 1e-10,
+      FP64; log det per evaluation;
+    posterior2048: Q_p = 0.1 I - Lap + 4 diag(mask) on 2048 x 2048 (10 % observed, seeded),
+      distance 4, N = 20, gradient (kappa^2, tau) per evaluation, mixed precision with
+      reliable updates (tol 1e-9) and the plain FP64 form beside it."""
+    import torch
+    import paper_1105_5256_gb300 as L
+    torch.cuda.set_device(0)
+    L.library(build_if_missing=True)
+    peak, src = peak_hbm()
+    # periodic 64^2, FP64
+    dims, k2 = (64, 64), 0.5
+    ctx = L.ld_create(L.grid_matrix(L.LD_STENCIL_2D5, dims, k2, periodic=True), 4, 20, 1e-10,
+                      L.options(precision=L.LD_FP64))
+    for _ in range(args.warmup):
+        L.ld_logdet(ctx)
+    ms = 0.0
+    for _ in range(args.steps):
+        v, info = L.ld_logdet(ctx)
+        ms += info["ms"]
+    print(json.dumps({"metric": "log-det evals/sec (64^2 periodic 5-point, d=4, N=20, FP64)",
+                      "value": args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                      "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": "periodic 64x64, kappa^2 0.5, d=4, N=20, tol 1e-10",
+                                 "n_colours": info["n_colours"], "iters": info["iters"],
+                                 "engine": info["engine"]},
+                      "logdet": v, "quad_cert": info["quad_cert"]}),
+          flush=True)
+    # 2048^2 Gauss-linear posterior with gradient
+    dims, k2, tau = (2048, 2048), 0.1, 4.0
+    n = dims[0] * dims[1]
+    mask = synth.obs_mask(4, n, 0.1)
+    out = {}
+    for name, prec, tol, delta in (("mixed", L.LD_MIXED, 1e-9, 1e-2), ("fp64", L.LD_FP64, 1e-9, 0.0)):
+        ctx = L.ld_create(L.grid_matrix(L.LD_STENCIL_2D5, dims, k2, tau=tau, obs_mask=mask), 4, 20, tol,
+                          L.options(precision=prec, reliable_delta=delta))
+        for _ in range(max(1, args.warmup // 3)):
+            L.ld_logdet_grad(ctx, [L.LD_P_KAPPA2, L.LD_P_TAU])
+        ms, it_ms, tile_iters, passes = 0.0, 0.0, 0, 0
+        for _ in range(args.steps):
+            v, g, info = L.ld_logdet_grad(ctx, [L.LD_P_KAPPA2, L.LD_P_TAU])
+            ms += info["ms"]
+            it_ms += info["iter_ms"]
+            tile_iters += info["tile_iters"]
+            passes += info["iters"]
+        out[name] = (v, g, info, ms, it_ms, tile_iters, passes)
+        del ctx
+    v, g, info, ms, it_ms, tile_iters, passes = out["mixed"]
+    T = info["tile_width"]
+    alg = 8 * n * T * 4 * tile_iters + (4 + 4) * n * passes     # r, w, p, x_lo in and out; colour, diag
+    vf, gf, infof, msf = out["fp64"][:4]
+    print(json.dumps({"metric": "log-det+grad evals/sec (2048^2 Gauss-linear posterior, d=4, N=20)",
+                      "value": args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                      "higher_is_better": True, "dtype": "f32 vectors / f64 scalars", "data": "synthetic",
+                      "config": {"workload": "2048x2048, kappa^2 0.1, tau 4, 10% mask, grad (kappa^2, tau), tol 1e-9",
+                                 "n_colours": info["n_colours"], "tile_width": T, "iters": info["iters"],
+                                 "reliable_updates": info["reliable_updates"],
+                                 "rel_resid_max": info["rel_resid_max"]},
+                      "roofline": {"bound": "hbm", "kernel": "fused CG pass (k_stream2d, 5-point)",
+                                   "achieved": alg / (it_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                                   "frac": alg / (it_ms / 1e3) / 1e9 / peak, "traffic": None,
+                                   "peak_source": src},
+                      "fp64_form": {"value": args.steps / (msf / 1e3), "rel_resid_max": infof["rel_resid_max"],
+                                    "logdet_rel_diff": abs(v - vf) / abs(vf),
+                                    "grad_rel_diff": [abs(a - b) / abs(b) for a, b in zip(g, gf)]}}),
+          flush=True)
+
+
 def run_field3d(args):
     """Secondary workload: Dirichlet 256^3, 7-point, seeded kappa^2 field, distance-6
     colouring, N = 32, tol 1e-6, mixed precision; one evaluation = log det and its
@@ -452,7 +524,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=BATCH, help="kappa^2 values per step")
     ap.add_argument("--tile-width", type=int, default=0, help="probing vectors per tile (0 = auto)")
-    ap.add_argument("--workload", default="matern1024", choices=["matern1024", "batch256", "field3d256"])
+    ap.add_argument("--workload", default="matern1024",
+                    choices=["matern1024", "batch256", "field3d256", "small"])
     ap.add_argument("--side", type=int, default=256, help="field3d256 workload: grid side")
     ap.add_argument("--fp64-sample", type=int, default=2,
                     help="draws also evaluated in the plain FP64 form (mixed precision runs)")
@@ -465,6 +538,8 @@ def main():
         run_batch(args)
     elif args.workload == "field3d256":
         run_field3d(args)
+    elif args.workload == "small":
+        run_small_configs(args)
     else:
         run_ours(args)
 
