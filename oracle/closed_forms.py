@@ -133,3 +133,21 @@ def quadratic_forms(kind, dims, kappa2, periodic, Z: np.ndarray, f=np.log, scale
     Z = np.asarray(Z)
     return np.array([float(np.sum(flam * spectral_coeffs(Z[:, k].reshape(shape), periodic)))
                      for k in range(Z.shape[1])])
+
+
+def apply_function(kind, dims, kappa2, periodic, V: np.ndarray, f, scale=1.0) -> np.ndarray:
+    """f(Q) V exactly for the columns of V (n x s): U diag(f(lambda)) U^T V with U the
+    orthonormal DST-I (Dirichlet) or DFT (periodic) basis of the grid."""
+    dims = [int(d) for d in dims]
+    shape = tuple(reversed(dims))
+    flam = f(eig_grid(kind, dims, kappa2, periodic, scale))
+    V = np.asarray(V, dtype=np.float64)
+    out = np.empty_like(V)
+    for k in range(V.shape[1]):
+        v = V[:, k].reshape(shape)
+        if periodic:
+            y = sfft.ifftn(flam * sfft.fftn(v, norm="ortho"), norm="ortho").real
+        else:
+            y = sfft.idstn(flam * sfft.dstn(v, type=1, norm="ortho"), type=1, norm="ortho")
+        out[:, k] = y.reshape(-1)
+    return out

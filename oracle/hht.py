@@ -82,3 +82,36 @@ def certificate(lmin: float, lmax: float, sigma, alpha, samples: int = 4001) -> 
 def rate_bound(lmin: float, lmax: float, N: int) -> float:
     """exp(-2 pi^2 N / (log(M/m) + 6)), the square-root method's rate."""
     return float(np.exp(-2.0 * np.pi ** 2 * N / (np.log(lmax / lmin) + 6.0)))
+
+
+# ---------------------------------------------------------------- inverse square root
+# Same contour and quadrature with f(z) = z^{-1/2}: after z = w^2 the integrand
+# f(w^2) 2w (w^2 I - A)^{-1} = 2 (w^2 I - A)^{-1} (principal branch, Re w > 0), so
+#   A^{-1/2} v ~ Re sum_j beta_j (A - sigma_j I)^{-1} v,  beta_j = -(2 i h / pi) w'(t_j),
+# with the nodes sigma_j of log_nodes.  Used to draw x = Q^{-1/2} z ~ N(0, Q^{-1}).
+
+def invsqrt_nodes(lmin: float, lmax: float, N: int):
+    """(sigma, beta) for z^{-1/2} on [lmin, lmax] (same sigma as log_nodes)."""
+    if not (0 < lmin <= lmax) or N < 1:
+        raise ValueError("need 0 < lmin <= lmax and N >= 1")
+    a, b = np.sqrt(lmin), np.sqrt(lmax)
+    r = np.sqrt(b / a)
+    k = (r - 1.0) / (r + 1.0)
+    if k <= 0.0:
+        raise ValueError("degenerate interval: lmin == lmax")
+    m = k * k
+    K = special.ellipk(m)
+    Kp = special.ellipk(1.0 - m)
+    h = 2.0 * K / N
+    x = -K + (np.arange(1, N + 1) - 0.5) * h
+    sn, cn, dn = jacobi_complex(x, Kp / 2.0, m)
+    g = np.sqrt(a * b)
+    w = g * (1.0 / k + sn) / (1.0 / k - sn)
+    dw = g * (2.0 / k) * cn * dn / (1.0 / k - sn) ** 2
+    return w * w, -(2j * h / np.pi) * dw
+
+
+def invsqrt_certificate(lmin: float, lmax: float, sigma, beta, samples: int = 4001) -> float:
+    """max |f_N(lambda) sqrt(lambda) - 1| (relative error) over [lmin, lmax]."""
+    lam = np.exp(np.linspace(np.log(lmin), np.log(lmax), samples))
+    return float(np.max(np.abs(f_N(lam, sigma, beta) * np.sqrt(lam) - 1.0)))

@@ -175,3 +175,17 @@ def logdet_method(Q: sp.csr_matrix, colour: np.ndarray, lmin: float, lmax: float
         out["terms"] = terms
         out["gterms"] = gterms
     return out
+
+
+# ---------------------------------------------------------------- likelihood (Sec. 1, 3)
+def gaussian_loglik(Q: sp.csr_matrix, Y: np.ndarray) -> float:
+    """sum over the columns y of Y of log N(y | 0, Q^{-1}) = 1/2 log det Q - 1/2 y^T Q y
+    - n/2 log(2 pi), with log det Q by the band Cholesky (the directly observed field
+    of Sec. 3)."""
+    Y = np.asarray(Y)
+    if Y.ndim == 1:
+        Y = Y[:, None]
+    n, s = Y.shape
+    ld = exact_logdet_band(Q)
+    quad = float(np.sum(Y * (Q @ Y)))
+    return 0.5 * s * ld - 0.5 * quad - 0.5 * s * n * np.log(2.0 * np.pi)

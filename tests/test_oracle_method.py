@@ -276,3 +276,41 @@ def test_hutchinson_is_unbiased_on_average():
     q = cf.quadratic_forms(om.KIND_2D5, dims, 0.5, True, Z)
     exact = cf.logdet(om.KIND_2D5, dims, 0.5, True)
     assert abs(q.mean() - exact) <= 4 * q.std() / np.sqrt(q.size)
+
+
+
+# ---------------------------------------------------------------- sampling and likelihood
+@pytest.mark.parametrize("N", [16, 24])
+def test_invsqrt_nodes_match_dense_inverse_sqrt(N):
+    g = np.random.default_rng(5)
+    B = g.standard_normal((30, 30))
+    A = B @ B.T / 30 + 0.2 * np.eye(30)
+    lam, U = np.linalg.eigh(A)
+    s, b = hht.invsqrt_nodes(lam.min(), lam.max(), N)
+    F = sum(np.real(bb * np.linalg.inv(A - ss * np.eye(30))) for ss, bb in zip(s, b))
+    ref = U @ np.diag(lam ** -0.5) @ U.T
+    cert = hht.invsqrt_certificate(lam.min(), lam.max(), s, b)
+    assert np.abs(F - ref).max() <= 10 * cert * np.abs(ref).max() + 1e-13
+    assert cert <= 200 * hht.rate_bound(lam.min(), lam.max(), N) + 1e-15
+    # same poles as the log approximation
+    s2, _ = hht.log_nodes(lam.min(), lam.max(), N)
+    assert np.allclose(s, s2, rtol=0, atol=1e-14 * np.abs(s2).max())
+
+
+def test_apply_function_matches_dense():
+    dims = (9, 7)
+    Q = om.precision(om.KIND_2D13_SQ, dims, 0.3)
+    lam, U = np.linalg.eigh(Q.toarray())
+    V = np.random.default_rng(2).standard_normal((63, 3))
+    ref = U @ np.diag(lam ** -0.5) @ U.T @ V
+    got = cf.apply_function(om.KIND_2D13_SQ, dims, 0.3, False, V, lambda x: x ** -0.5)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_gaussian_loglik_matches_dense_formula():
+    from scipy.stats import multivariate_normal
+    dims = (6, 5)
+    Q = om.precision(om.KIND_2D5, dims, 0.7, scale=2.0)
+    Y = np.random.default_rng(8).standard_normal((30, 2))
+    ref = sum(multivariate_normal(np.zeros(30), np.linalg.inv(Q.toarray())).logpdf(Y[:, k]) for k in range(2))
+    assert abs(mt.gaussian_loglik(Q, Y) - ref) <= 1e-10 * abs(ref)
