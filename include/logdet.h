@@ -200,6 +200,12 @@ ld_status ld_apply(ld_ctx *ctx, int ncols, const double *x, double *y);
  * device memory for the call.  Errors as ld_logdet. */
 ld_status ld_logmv(ld_ctx *ctx, int ncols, const double *V, double *Y, ld_info *info);
 
+/* Q^{-1/2} V for the columns of V (n x ncols, row-major, FP64), by the same contour,
+ * nodes and shifted solves as ld_logmv with the weights of z^{-1/2} (the paper has no
+ * sampler; this draws x = Q^{-1/2} z ~ N(0, Q^{-1}) for standard normal z, the synthetic
+ * fields a likelihood fit of Sec. 3 needs).  Errors as ld_logmv. */
+ld_status ld_invsqrt_mv(ld_ctx *ctx, int ncols, const double *V, double *Y, ld_info *info);
+
 /* Colouring distance by decay (Sec. 2.1, the heuristic for the power p of Q^p): forms
  * y = log(Q) e_j with the context's method (as ld_logmv: the context's operator, nodes,
  * tolerance and precision) and returns *distance = min { d(l, j) : |y_l| < eps |y_j| },

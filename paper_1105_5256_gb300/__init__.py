@@ -98,6 +98,7 @@ def library(build_if_missing: bool = False):
         "ld_select_distance": ([vp, i64, dbl, C.c_int, P(i32), vp, P(Info)], st),
         "ld_hutchinson": ([vp, C.c_int, vp, P(dbl), P(dbl), vp, P(Info)], st),
         "ld_wait_selftest": ([i64], st),
+        "ld_invsqrt_mv": ([vp, C.c_int, vp, vp, P(Info)], st),
         "ld_colour_csr": ([i64, vp, vp, C.c_int, vp, P(i32)], st),
         "ld_colour_grid": ([C.c_int, vp, C.c_int, C.c_int, vp, P(i32)], st),
         "ld_hht_nodes": ([dbl, dbl, C.c_int, vp, vp, P(dbl)], st),
@@ -313,6 +314,17 @@ def ld_hutchinson(ctx: Context, Z: np.ndarray):
     _check(library().ld_hutchinson(ctx.handle, Z.shape[1], _ptr(Z), C.byref(est), C.byref(se),
                                    _ptr(q), C.byref(info)))
     return est.value, se.value, q, info.as_dict()
+
+
+def ld_invsqrt_mv(ctx: Context, V: np.ndarray):
+    """Q^{-1/2} V for an n x k block; returns (Y, info)."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    if V.ndim == 1:
+        V = V[:, None]
+    Y = np.zeros_like(V)
+    info = Info()
+    _check(library().ld_invsqrt_mv(ctx.handle, V.shape[1], _ptr(V), _ptr(Y), C.byref(info)))
+    return Y, info.as_dict()
 
 
 def ld_select_distance(ctx: Context, j: int, eps: float, max_d: int = 32):

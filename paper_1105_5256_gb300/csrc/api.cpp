@@ -1020,7 +1020,10 @@ ld_status ld_apply(ld_ctx *c, int ncols, const double *x, double *y) {
     return LD_OK;
 }
 
-ld_status ld_logmv(ld_ctx *c, int ncols, const double *V, double *Y, ld_info *info) {
+// f(Q) V by the vector form of CG-M, for the rational f whose weights (N double2, on the
+// device) pair with the context's shifts: log (the context's weights) or z^{-1/2}
+static ld_status funmv(ld_ctx *c, int ncols, const double *V, double *Y, ld_info *info,
+                       const double2 *weight_dev) {
     if (!c || !V || !Y || ncols < 1) return fail(LD_EINVAL, "bad arguments");
     if (c->is_batch) return fail(LD_EINVAL, "batched context");
     const int T = c->T, N = c->nshift;
@@ -1058,6 +1061,10 @@ ld_status ld_logmv(ld_ctx *c, int ncols, const double *V, double *Y, ld_info *in
     s.ncols = C;
     s.keep_x0 = 0;
     s.x = nullptr;
+    s.xhi = nullptr;
+    s.weight = weight_dev;
+    s.tile0 = 0;
+    s.tstride = 1;
     for (int k = 0; k < 2; ++k) {
         s.rbuf[k] = vec[k].p;
         s.wbuf[k] = vec[2 + k].p;
@@ -1122,6 +1129,25 @@ ld_status ld_logmv(ld_ctx *c, int ncols, const double *V, double *Y, ld_info *in
                 if (col < ncols) Y[i * ncols + col] = hy[((size_t)t * n + i) * T + k];
             }
     return LD_OK;
+}
+
+ld_status ld_logmv(ld_ctx *c, int ncols, const double *V, double *Y, ld_info *info) {
+    if (!c) return fail(LD_EINVAL, "bad arguments");
+    return funmv(c, ncols, V, Y, info, c->s.weight);
+}
+
+ld_status ld_invsqrt_mv(ld_ctx *c, int ncols, const double *V, double *Y, ld_info *info) {
+    if (!c) return fail(LD_EINVAL, "bad arguments");
+    if (c->is_batch) return fail(LD_EINVAL, "batched context");
+    std::vector<std::complex<double>> sg(c->nshift), be(c->nshift);
+    if (ld::hht_invsqrt_nodes(c->lmin, c->lmax, c->nshift, sg.data(), be.data()) != 0)
+        return fail(LD_EINVAL, "bad spectral interval [%g, %g]", c->lmin, c->lmax);
+    std::vector<double2> hw(c->nshift);
+    for (int l = 0; l < c->nshift; ++l) hw[l] = make_double2(be[l].real(), be[l].imag());
+    DevBuf wd;
+    CUDA_TRY(wd.alloc(hw.size() * sizeof(double2)));
+    CUDA_TRY(cudaMemcpy(wd.p, hw.data(), hw.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    return funmv(c, ncols, V, Y, info, wd.as<double2>());
 }
 
 ld_status ld_wait_selftest(int64_t limit_ns) {

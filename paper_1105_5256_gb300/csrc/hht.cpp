@@ -102,6 +102,35 @@ int hht_log_nodes(double lmin, double lmax, int N, std::complex<double> *sigma,
     return 0;
 }
 
+// The same contour and nodes for f(z) = z^{-1/2}: after z = w^2 the integrand is
+// 2 (w^2 I - Q)^{-1} (principal branch, Re w > 0), so
+//   Q^{-1/2} v ~ Re sum_j beta_j (Q - sigma_j I)^{-1} v,  beta_j = -(2 i h / pi) w'(t_j).
+int hht_invsqrt_nodes(double lmin, double lmax, int N, std::complex<double> *sigma,
+                      std::complex<double> *beta) {
+    if (!(lmin > 0.0) || !(lmax >= lmin) || N < 1) return -1;
+    const double a = std::sqrt(lmin), b = std::sqrt(lmax);
+    const double r = std::sqrt(b / a);
+    const double k = (r - 1.0) / (r + 1.0);
+    if (!(k > 0.0)) return -1;
+    const double m = k * k;
+    const double K = ellip_k(m);
+    const double Kp = ellip_k(1.0 - m);
+    const double h = 2.0 * K / N;
+    const double g = std::sqrt(a * b);
+    const std::complex<double> I(0.0, 1.0);
+    for (int j = 0; j < N; ++j) {
+        double x = -K + (j + 0.5) * h;
+        std::complex<double> sn, cn, dn;
+        jacobi_complex(x, 0.5 * Kp, m, &sn, &cn, &dn);
+        std::complex<double> den = 1.0 / k - sn;
+        std::complex<double> w = g * (1.0 / k + sn) / den;
+        std::complex<double> dw = g * (2.0 / k) * cn * dn / (den * den);
+        sigma[j] = w * w;
+        beta[j] = -(2.0 * h / M_PI) * I * dw;
+    }
+    return 0;
+}
+
 double hht_certificate(double lmin, double lmax, int N, const std::complex<double> *sigma,
                        const std::complex<double> *alpha) {
     const int S = 2001;

@@ -19,6 +19,8 @@ double ellip_k(double m);
 void jacobi_real(double u, double m, double *sn, double *cn, double *dn);
 int hht_log_nodes(double lmin, double lmax, int N, std::complex<double> *sigma,
                   std::complex<double> *alpha);
+int hht_invsqrt_nodes(double lmin, double lmax, int N, std::complex<double> *sigma,
+                      std::complex<double> *beta);
 double hht_certificate(double lmin, double lmax, int N, const std::complex<double> *sigma,
                        const std::complex<double> *alpha);
 

@@ -1,0 +1,74 @@
+"""GPU: GMRF sampling by the rational inverse square root, and the likelihood fit of
+Sec. 3 driven by the probed log det.
+
+* ld_invsqrt_mv against the oracle's exact f(Q) V for the same rational function
+  (within the CG tolerance) and for lambda^{-1/2} itself (within its certificate);
+* a modified Newton fit of (kappa^2, s) to seeded synthetic fields, against the exact
+  maximum-likelihood estimate the oracle finds with band-Cholesky log dets: the
+  estimates approach it as the colouring distance grows (the trend of Table 1;
+  kappa^2 carries the probing bias of d log det / d kappa^2 = tr Q^{-1}).
+"""
+import numpy as np
+import pytest
+import scipy.optimize as so
+
+import paper_1105_5256_gb300 as L
+from paper_1105_5256_gb300 import fit as F
+import synth
+from oracle import closed_forms as cf
+from oracle import hht
+from oracle import matrices as om
+from oracle import method as mt
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1105_5256_gb300 import _build
+    _build.build()
+    return L.library()
+
+
+@pytest.mark.parametrize("kind,dims,per,k2", [(om.KIND_2D13_SQ, (48, 40), False, 0.1),
+                                              (om.KIND_2D5, (64, 64), True, 0.5)])
+def test_invsqrt_matches_oracle(kind, dims, per, k2):
+    N, tol = 24, 1e-11
+    ctx = L.ld_create(L.grid_matrix(kind, dims, k2, periodic=per), 1, N, tol,
+                      L.options(precision=L.LD_FP64))
+    n = int(np.prod(dims))
+    V = synth.random_probe_block(6, n, 3)
+    Y, info = L.ld_invsqrt_mv(ctx, V)
+    lo, hi = mt.spectral_bounds(kind, dims, k2, periodic=per)
+    s, b = hht.invsqrt_nodes(lo, hi, N)
+    rat = cf.apply_function(kind, dims, k2, per, V, lambda lam: hht.f_N(lam, s, b))
+    assert np.abs(Y - rat).max() <= 1e-8 * np.abs(rat).max()
+    exact = cf.apply_function(kind, dims, k2, per, V, lambda lam: lam ** -0.5)
+    cert = hht.invsqrt_certificate(lo, hi, s, b)
+    assert np.abs(Y - exact).max() <= (10 * cert + 1e-8) * np.abs(exact).max()
+
+
+def test_fit_approaches_exact_mle_with_distance():
+    kind, dims, k2_true, s_true, S = L.LD_STENCIL_2D5, (48, 48), 0.3, 2.0, 16
+    n = dims[0] * dims[1]
+    Y = F.sample(kind, dims, k2_true, s_true, synth.random_probe_block(9, n, S))
+
+    def neg(eta):
+        Q = om.precision(om.KIND_2D5, dims, float(np.exp(eta[0])), scale=float(np.exp(eta[1])))
+        return -mt.gaussian_loglik(Q, Y)
+    ref = so.minimize(neg, np.log([0.5, 1.0]), method="Nelder-Mead",
+                      options={"xatol": 1e-9, "fatol": 1e-10, "maxiter": 2000})
+    k2_mle, s_mle = np.exp(ref.x)
+    errs = {}
+    for d in (1, 4, 8, 16):
+        lik = F.Likelihood(kind, dims, Y, d)
+        out = F.fit(lik, 0.5, 1.0)
+        errs[d] = max(abs(out["kappa2"] - k2_mle) / k2_mle, abs(out["scale"] - s_mle) / s_mle)
+        print("distance %d: kappa2 %.5f scale %.5f (exact MLE %.5f %.5f, true %.2f %.2f) in %d iterations"
+              % (d, out["kappa2"], out["scale"], k2_mle, s_mle, k2_true, s_true, out["iterations"]))
+    print(errs)
+    assert errs[1] > errs[4] > errs[8] > errs[16]
+    assert errs[16] <= 0.05
