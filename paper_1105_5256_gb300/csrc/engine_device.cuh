@@ -813,20 +813,7 @@ __device__ __forceinline__ Pack<V, TS> diff5p(const Pack<V, TS> &c, const Pack<V
 }
 
 // (c p + sum of the four differences), the difference-form stencil of one level
-template <typename V, int TS>
-__device__ __forceinline__ Pack<V, TS> diff5(V c, const Pack<V, TS> &pc, const Pack<V, TS> &pl,
-                                             const Pack<V, TS> &pr, const Pack<V, TS> &pd,
-                                             const Pack<V, TS> &pu) {
-    Pack<V, TS> o;
-#pragma unroll
-    for (int t = 0; t < TS; ++t)
-        o.v[t] = fma(c, pc.v[t], ((pc.v[t] - pl.v[t]) + (pc.v[t] - pr.v[t])) +
-                                     ((pc.v[t] - pd.v[t]) + (pc.v[t] - pu.v[t])));
-    return o;
-}
-
 // resident CTAs per SM the register budget is sized for
-constexpr int stream_min_blocks(int G) { return G == 1 ? 3 : 2; }
 template <typename V, int T>
 __host__ __device__ constexpr int stream_min_blocks_t() { return sizeof(V) * T <= 8 ? 6 : (sizeof(V) * T <= 16 ? 5 : 3); }
 
@@ -902,12 +889,22 @@ __device__ __forceinline__ void stream_sweep(const Solve &s, int tile, int cur, 
 
     int y = ys - H;
     const int yend = ye + H;
-    // rows past the segment's last step are not needed: empty (zero-fill) group
-    auto load_row = [&](int yr, int slot) {
+    // Rows are loaded in order, so the vertex index of the next row to load advances
+    // by nx per row (wrapping on a torus) instead of being recomputed.
+    int lrow = y;
+    int64_t lvtx;
+    {
         bool iny;
-        const int gyw = wrap_coord(yr, ny, per, iny);
-        const bool in = iny && inx && yr < yend;
-        const int64_t e = in ? ((int64_t)gyw * nx + gxw) * T : 0;
+        const int w0 = wrap_coord(lrow, ny, per, iny);
+        lvtx = (per ? (int64_t)w0 : (int64_t)lrow) * nx + gxw;
+    }
+    const int64_t nvtx = (int64_t)nx * ny;
+    // rows past the segment's last step are not needed: empty (zero-fill) group
+    auto load_row = [&](int slot) {
+        const int yr = lrow;
+        const bool in = (per || (unsigned)yr < (unsigned)ny) && inx && yr < yend;
+        const int64_t vtx = in ? lvtx : 0;
+        const int64_t e = vtx * T;
         P *q = ring + slot * 3 * NT;
         cp_async_pack<V, TS>(q, r + e, in);
         cp_async_pack<V, TS>(q + NT, w + e, in);
@@ -915,10 +912,13 @@ __device__ __forceinline__ void stream_sweep(const Solve &s, int tile, int cur, 
         {
             const unsigned dc = (unsigned)__cvta_generic_to_shared(ringc + slot * NT);
             asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dc),
-                         "l"(s.colour + (in ? (int64_t)gyw * nx + gxw : 0)), "r"(in ? 4 : 0));
+                         "l"(s.colour + vtx), "r"(in ? 4 : 0));
         }
-        if (diag) cp_async_word<V>(ringd + slot * NT, diag + (in ? (int64_t)gyw * nx + gxw : 0), in);
+        if (diag) cp_async_word<V>(ringd + slot * NT, diag + vtx, in);
         cp_async_commit();
+        ++lrow;
+        lvtx += nx;
+        if (per && lvtx >= nvtx) lvtx -= nvtx;
     };
     // outputs at (gx, y) of lattice row y held in ring slot `slot`
     auto emit = [&](int y, int slot, const P &pk, const P &wk) {
@@ -957,7 +957,7 @@ __device__ __forceinline__ void stream_sweep(const Solve &s, int tile, int cur, 
     // copy group is always the (y - y0 + 1)-th: waiting with PD - H - 1 groups
     // pending completes it.
 #pragma unroll
-    for (int k = 0; k < PD - H; ++k) load_row(y + k, k);
+    for (int k = 0; k < PD - H; ++k) load_row(k);
     const P sc = M::splat(op_scale<V>(s.op)), k2 = M::splat(op_kappa2<V>(s.op));
     int slot = 0;            // slot of row y
     for (; y < yend; ++y) {
@@ -1001,8 +1001,8 @@ __device__ __forceinline__ void stream_sweep(const Solve &s, int tile, int cur, 
                 emit(y - 1, slot_h, pw1, wk);
             }
         }
-        // row y - H is done: its slot takes row y - H + PD
-        load_row(y - H + PD, slot_h);
+        // row y - H is done: its slot takes row y - H + PD (the next row in order)
+        load_row(slot_h);
         slot = slot + 1 == PD ? 0 : slot + 1;
         __syncthreads();
     }
