@@ -920,20 +920,20 @@ __device__ __forceinline__ void stream_sweep(const Solve &s, int tile, int cur, 
         lvtx += nx;
         if (per && lvtx >= nvtx) lvtx -= nvtx;
     };
-    // outputs at (gx, y) of lattice row y held in ring slot `slot`
-    auto emit = [&](int y, int slot, const P &pk, const P &wk) {
+    V *const rn = static_cast<V *>(cur ? s.rbuf[0] : s.rbuf[1]) + off;
+    V *const wn = static_cast<V *>(cur ? s.wbuf[0] : s.wbuf[1]) + off;
+    V *const pn = static_cast<V *>(cur ? s.pbuf[0] : s.pbuf[1]) + off;
+    V *const xs = KEEPX ? static_cast<V *>(s.x) + off : nullptr;
+    // outputs at vertex evtx (column gx of the row emitted this step), ring slot `slot`
+    auto emit = [&](int64_t evtx, int slot, const P &pk, const P &wk) {
         const P *q = ring + slot * 3 * NT;
         const P rk = M::fma(na, q[NT], q[0]);
-        const int64_t gi = (int64_t)y * nx + gx;
-        const int64_t e = gi * T;
-        V *rn = static_cast<V *>(cur ? s.rbuf[0] : s.rbuf[1]) + off;
-        V *wn = static_cast<V *>(cur ? s.wbuf[0] : s.wbuf[1]) + off;
-        V *pn = static_cast<V *>(cur ? s.pbuf[0] : s.pbuf[1]) + off;
+        const int64_t e = evtx * T;
         *reinterpret_cast<P *>(rn + e) = rk;
         *reinterpret_cast<P *>(pn + e) = pk;
         *reinterpret_cast<P *>(wn + e) = wk;
         if constexpr (KEEPX) {
-            V *x = static_cast<V *>(s.x) + off;
+            V *x = xs;
             const P xo = *reinterpret_cast<const P *>(x + e);
             *reinterpret_cast<P *>(x + e) = M::fma(M::neg(na), q[2 * NT], xo);
         }
@@ -959,6 +959,7 @@ __device__ __forceinline__ void stream_sweep(const Solve &s, int tile, int cur, 
 #pragma unroll
     for (int k = 0; k < PD - H; ++k) load_row(k);
     const P sc = M::splat(op_scale<V>(s.op)), k2 = M::splat(op_kappa2<V>(s.op));
+    int64_t evtx = (int64_t)(y - H) * nx + gx;   // vertex of row y - H in column gx
     int slot = 0;            // slot of row y
     for (; y < yend; ++y) {
         cp_async_wait<PD - 1 - H>();
@@ -975,8 +976,7 @@ __device__ __forceinline__ void stream_sweep(const Solve &s, int tile, int cur, 
             // u = Q1 p at (x, y-1): p row y-1 was shared last step
             if (y >= ys) {
                 P u = zero_pack<V, TS>();
-                bool uin;
-                wrap_coord(y - 1, ny, per, uin);
+                const bool uin = per || (unsigned)(y - 1) < (unsigned)ny;
                 if (uin && inx && xl >= 1 && xl < SW - 1) {
                     const P *row = ps + ((y - 1) & 1) * NT;
                     u = diff5p<V, TS>(k2, pw1, row[threadIdx.x - G], row[threadIdx.x + G], pw0, pw2);
@@ -990,7 +990,7 @@ __device__ __forceinline__ void stream_sweep(const Solve &s, int tile, int cur, 
             if (y - 2 >= ys && y - 2 < ye && outx) {
                 const P *row = us + ((y - 2) & 1) * NT;
                 const P wk = M::mul(sc, diff5p<V, TS>(k2, uw1, row[threadIdx.x - G], row[threadIdx.x + G], uw0, uw2));
-                emit(y - 2, slot_h, pw0, wk);
+                emit(evtx, slot_h, pw0, wk);
             }
         } else {
             // w = Q p at (x, y-1): p row y-1 was shared last step
@@ -998,11 +998,12 @@ __device__ __forceinline__ void stream_sweep(const Solve &s, int tile, int cur, 
                 const V dg = diag ? ringd[slot_h * NT] : op_kappa2<V>(s.op);
                 const P *row = ps + ((y - 1) & 1) * NT;
                 const P wk = M::mul(sc, diff5p<V, TS>(M::splat(dg), pw1, row[threadIdx.x - G], row[threadIdx.x + G], pw0, pw2));
-                emit(y - 1, slot_h, pw1, wk);
+                emit(evtx, slot_h, pw1, wk);
             }
         }
         // row y - H is done: its slot takes row y - H + PD (the next row in order)
         load_row(slot_h);
+        evtx += nx;
         slot = slot + 1 == PD ? 0 : slot + 1;
         __syncthreads();
     }
