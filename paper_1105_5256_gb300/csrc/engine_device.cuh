@@ -924,6 +924,7 @@ __device__ __forceinline__ void stream_sweep(const Solve &s, int tile, int cur, 
     V *const wn = static_cast<V *>(cur ? s.wbuf[0] : s.wbuf[1]) + off;
     V *const pn = static_cast<V *>(cur ? s.pbuf[0] : s.pbuf[1]) + off;
     V *const xs = KEEPX ? static_cast<V *>(s.x) + off : nullptr;
+    P xpre = zero_pack<V, TS>();   // x of the row emitted next step, loaded a step ahead
     // outputs at vertex evtx (column gx of the row emitted this step), ring slot `slot`
     auto emit = [&](int64_t evtx, int slot, const P &pk, const P &wk) {
         const P *q = ring + slot * 3 * NT;
@@ -932,11 +933,7 @@ __device__ __forceinline__ void stream_sweep(const Solve &s, int tile, int cur, 
         *reinterpret_cast<P *>(rn + e) = rk;
         *reinterpret_cast<P *>(pn + e) = pk;
         *reinterpret_cast<P *>(wn + e) = wk;
-        if constexpr (KEEPX) {
-            V *x = xs;
-            const P xo = *reinterpret_cast<const P *>(x + e);
-            *reinterpret_cast<P *>(x + e) = M::fma(M::neg(na), q[2 * NT], xo);
-        }
+        if constexpr (KEEPX) *reinterpret_cast<P *>(xs + e) = M::fma(M::neg(na), q[2 * NT], xpre);
         const int lc = ringc[slot * NT] - cb;
         acc.rr = M::fma(rk, rk, acc.rr);
         acc.pw = M::fma(pk, wk, acc.pw);
@@ -1004,6 +1001,10 @@ __device__ __forceinline__ void stream_sweep(const Solve &s, int tile, int cur, 
         // row y - H is done: its slot takes row y - H + PD (the next row in order)
         load_row(slot_h);
         evtx += nx;
+        if constexpr (KEEPX) {
+            const int yo = y + 1 - H;       // row emitted by the next step
+            if (yo >= ys && yo < ye && outx) xpre = *reinterpret_cast<const P *>(xs + evtx * T);
+        }
         slot = slot + 1 == PD ? 0 : slot + 1;
         __syncthreads();
     }
@@ -1397,6 +1398,7 @@ __global__ void __launch_bounds__(P3T, stream3d_min_blocks<V, T>()) k_stream3d(S
         cp_async_commit();
     };
     P pw0 = zero_pack<V, T>(), pw1 = pw0, pw2 = pw0;   // p at planes z-2, z-1, z
+    P xpre = zero_pack<V, T>();   // x of the plane emitted next step, loaded a step ahead
     const P sc = M::splat(op_scale<V>(s.op));
     // ring slot of plane zr is (zr - z0) mod PD (see the 2D sweep for the schedule)
 #pragma unroll
@@ -1429,11 +1431,8 @@ __global__ void __launch_bounds__(P3T, stream3d_min_blocks<V, T>()) k_stream3d(S
             *reinterpret_cast<P *>(static_cast<V *>(cur ? s.rbuf[0] : s.rbuf[1]) + off + e) = rk;
             *reinterpret_cast<P *>(static_cast<V *>(cur ? s.pbuf[0] : s.pbuf[1]) + off + e) = c;
             *reinterpret_cast<P *>(static_cast<V *>(cur ? s.wbuf[0] : s.wbuf[1]) + off + e) = wk;
-            if constexpr (KEEPX) {
-                V *x = static_cast<V *>(s.x) + off;
-                const P xo = *reinterpret_cast<const P *>(x + e);
-                *reinterpret_cast<P *>(x + e) = M::fma(M::neg(na), q[2 * P3T], xo);
-            }
+            if constexpr (KEEPX)
+                *reinterpret_cast<P *>(static_cast<V *>(s.x) + off + e) = M::fma(M::neg(na), q[2 * P3T], xpre);
             const int lc = ringc[slot_h * P3T] - cb;
             acc.rr = M::fma(rk, rk, acc.rr);
             acc.pw = M::fma(c, wk, acc.pw);
@@ -1448,6 +1447,11 @@ __global__ void __launch_bounds__(P3T, stream3d_min_blocks<V, T>()) k_stream3d(S
             }
         }
         load_plane(z - H + PD, slot_h);
+        if constexpr (KEEPX) {
+            if (z >= zs && z < ze && out)   // plane z is emitted by the next step
+                xpre = *reinterpret_cast<const P *>(static_cast<const V *>(s.x) + off +
+                                                    ((int64_t)z * plane + (int64_t)gy * nx + gx) * T);
+        }
         slot = slot + 1 == PD ? 0 : slot + 1;
         __syncthreads();
     }
