@@ -5,6 +5,7 @@
 // "eq_rat_app"), device buffers, the CG iteration driver (CUDA-graph chunks
 // with an on-device convergence counter) and the gradient pass.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <complex>
 #include <cstdarg>
@@ -129,6 +130,8 @@ struct ld_ctx {
     std::vector<ld_ctx *> subs;
     DevBuf d_solves, d_items, d_queue, d_bout, d_bint;
     int nitems = 0, bgrid = 0;
+    // batch: instances in the persistent launch (small) and on the multi-CTA engine (large)
+    std::vector<int> small_idx, large_idx;
     cudaGraphExec_t bgraph = nullptr;
 
     ~ld_ctx() {
@@ -1301,74 +1304,88 @@ ld_status ld_batch_create(int count, const ld_matrix *Qs, const int *distances, 
     }
     CUDA_TRY(cudaEventCreate(&c->ev0));
     CUDA_TRY(cudaEventCreate(&c->ev1));
-    // every instance: a one-CTA-per-tile context with a common tile width
+    // Every instance gets a context with a common tile width.  A tile in the persistent
+    // launch is one CTA's whole solve, so an instance whose solve would outlast the rest
+    // of the batch (CG iterations ~ 8 sqrt(cond), a lattice row of 128 vertices per CTA
+    // step of about a microsecond: more than 0.4 s) runs on the multi-CTA grid engine
+    // instead, on its own stream beside the persistent launch.
     ld_options sub = opt;
-    sub.engine = 2;
     sub.keep_x0 = 0;
     sub.colouring = nullptr;
-    sub.cuda_stream = c->stream;
     if (sub.tile_width == 0) sub.tile_width = opt.precision == LD_MIXED ? 2 : 1;
     c->T = sub.tile_width;
     c->subs.reserve(count);
     for (int i = 0; i < count; ++i) {
         if (Qs[i].kind == LD_CSR) return fail(LD_EUNSUPPORTED, "batched instances are grid kinds");
+        double lo = 0.0, hi = 0.0;
+        if (ld_status st = ld_grid_bounds(&Qs[i], &lo, &hi)) return st;
+        int32_t dd[3] = {Qs[i].dims[0], Qs[i].dims[1], Qs[i].kind == LD_STENCIL_3D7 ? Qs[i].dims[2] : 1};
+        const double est_s = 8.0 * std::sqrt(hi / lo) * ((double)grid_n(dd) / 128.0) * 1.2e-6;
+        const bool large = est_s > 0.4 && grid_n(dd) >= 32768;
+        ld_options o = sub;
+        o.engine = large ? 1 : 2;
+        o.cuda_stream = large ? nullptr : c->stream;
         ld_ctx *sc = nullptr;
-        ld_status st = ld_create(&Qs[i], distances[i], n_shifts, tol, &sub, &sc);
+        ld_status st = ld_create(&Qs[i], distances[i], n_shifts, tol, &o, &sc);
         if (st != LD_OK) {
             std::string msg = g_err;
             return fail(st, "instance %d: %s", i, msg.c_str());
         }
         c->subs.push_back(sc);
+        (large ? c->large_idx : c->small_idx).push_back(i);
     }
-    // device table of the instances' solves and the work items, longest first
-    std::vector<Solve> solves(count);
-    std::vector<int> ncol(count);
+    // device table of the small instances' solves and their work items, longest first
+    const int nsmall = (int)c->small_idx.size();
+    std::vector<Solve> solves(std::max(nsmall, 1));
+    std::vector<int> ncol(std::max(nsmall, 1));
     struct Item { double cost; int inst, tile; };
     std::vector<Item> items;
-    for (int i = 0; i < count; ++i) {
-        const ld_ctx *sc = c->subs[i];
-        solves[i] = sc->s;
-        ncol[i] = sc->ncolours;
+    for (int k = 0; k < nsmall; ++k) {
+        const ld_ctx *sc = c->subs[c->small_idx[k]];
+        solves[k] = sc->s;
+        ncol[k] = sc->ncolours;
         const double cost = (double)sc->n * std::sqrt(sc->lmax / sc->lmin);
-        for (int t = 0; t < sc->ntiles; ++t) items.push_back({cost, i, t});
+        for (int t = 0; t < sc->ntiles; ++t) items.push_back({cost, k, t});
     }
     std::stable_sort(items.begin(), items.end(), [](const Item &x, const Item &y) { return x.cost > y.cost; });
-    std::vector<int2> hitems(items.size());
-    for (size_t k = 0; k < items.size(); ++k) hitems[k] = make_int2(items[k].inst, items[k].tile);
-    c->nitems = (int)items.size();
-    CUDA_TRY(c->d_solves.alloc(sizeof(Solve) * count));
-    CUDA_TRY(cudaMemcpy(c->d_solves.p, solves.data(), sizeof(Solve) * count, cudaMemcpyHostToDevice));
-    CUDA_TRY(c->d_items.alloc(sizeof(int2) * hitems.size()));
-    CUDA_TRY(cudaMemcpy(c->d_items.p, hitems.data(), sizeof(int2) * hitems.size(), cudaMemcpyHostToDevice));
-    CUDA_TRY(c->d_queue.alloc(sizeof(int)));
-    CUDA_TRY(c->d_bout.alloc(sizeof(double) * 2 * count));
-    CUDA_TRY(c->d_bint.alloc(sizeof(int) * 3 * count));
-    CUDA_TRY(cudaMemcpy(c->d_bint.as<int>() + 2 * count, ncol.data(), sizeof(int) * count, cudaMemcpyHostToDevice));
-    int dev = 0, sms = 152;
-    CUDA_TRY(cudaGetDevice(&dev));
-    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int occ = ld::engine_batch_occupancy(opt.precision == LD_MIXED ? 1 : 0, c->T);
-    c->bgrid = std::max(1, std::min(c->nitems, occ * sms));
-    // one CUDA graph: queue reset, per-instance prep, the persistent solve, per-instance sums
-    const int max_iter = opt.max_iter > 0 ? opt.max_iter : 100000;
-    cudaGraph_t g = nullptr;
-    CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    const int err = ld::engine_batch(c->d_solves.as<Solve>(), c->d_bint.as<int>() + 2 * count, count,
-                                     c->d_items.as<int2>(), c->nitems, c->d_queue.as<int>(), max_iter,
-                                     opt.precision == LD_MIXED ? 1 : 0, c->T, c->bgrid,
-                                     c->d_bout.as<double>(), c->d_bout.as<double>() + count,
-                                     c->d_bint.as<int>(), c->d_bint.as<int>() + count, c->stream);
-    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
-    if (err) {
-        if (g) cudaGraphDestroy(g);
-        return fail(LD_ECUDA, "batch capture: %s", ld::engine_error_string(err));
-    }
-    if (e2 != cudaSuccess) return fail(LD_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e2));
-    cudaError_t e3 = cudaGraphInstantiate(&c->bgraph, g, 0);
-    cudaGraphDestroy(g);
-    if (e3 != cudaSuccess) {
-        c->bgraph = nullptr;
-        return fail(LD_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e3));
+    if (nsmall > 0) {
+        std::vector<int2> hitems(items.size());
+        for (size_t k = 0; k < items.size(); ++k) hitems[k] = make_int2(items[k].inst, items[k].tile);
+        c->nitems = (int)items.size();
+        CUDA_TRY(c->d_solves.alloc(sizeof(Solve) * nsmall));
+        CUDA_TRY(cudaMemcpy(c->d_solves.p, solves.data(), sizeof(Solve) * nsmall, cudaMemcpyHostToDevice));
+        CUDA_TRY(c->d_items.alloc(sizeof(int2) * hitems.size()));
+        CUDA_TRY(cudaMemcpy(c->d_items.p, hitems.data(), sizeof(int2) * hitems.size(), cudaMemcpyHostToDevice));
+        CUDA_TRY(c->d_queue.alloc(sizeof(int)));
+        CUDA_TRY(c->d_bout.alloc(sizeof(double) * 2 * nsmall));
+        CUDA_TRY(c->d_bint.alloc(sizeof(int) * 3 * nsmall));
+        CUDA_TRY(cudaMemcpy(c->d_bint.as<int>() + 2 * nsmall, ncol.data(), sizeof(int) * nsmall, cudaMemcpyHostToDevice));
+        int dev = 0, sms = 152;
+        CUDA_TRY(cudaGetDevice(&dev));
+        CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int occ = ld::engine_batch_occupancy(opt.precision == LD_MIXED ? 1 : 0, c->T);
+        c->bgrid = std::max(1, std::min(c->nitems, occ * sms));
+        // one CUDA graph: queue reset, per-instance prep, the persistent solve, per-instance sums
+        const int max_iter = opt.max_iter > 0 ? opt.max_iter : 100000;
+        cudaGraph_t g = nullptr;
+        CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        const int err = ld::engine_batch(c->d_solves.as<Solve>(), c->d_bint.as<int>() + 2 * nsmall, nsmall,
+                                         c->d_items.as<int2>(), c->nitems, c->d_queue.as<int>(), max_iter,
+                                         opt.precision == LD_MIXED ? 1 : 0, c->T, c->bgrid,
+                                         c->d_bout.as<double>(), c->d_bout.as<double>() + nsmall,
+                                         c->d_bint.as<int>(), c->d_bint.as<int>() + nsmall, c->stream);
+        cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+        if (err) {
+            if (g) cudaGraphDestroy(g);
+            return fail(LD_ECUDA, "batch capture: %s", ld::engine_error_string(err));
+        }
+        if (e2 != cudaSuccess) return fail(LD_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e2));
+        cudaError_t e3 = cudaGraphInstantiate(&c->bgraph, g, 0);
+        cudaGraphDestroy(g);
+        if (e3 != cudaSuccess) {
+            c->bgraph = nullptr;
+            return fail(LD_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e3));
+        }
     }
     *out = guard.release();
     return LD_OK;
@@ -1378,22 +1395,46 @@ ld_status ld_batch_logdet(ld_ctx *c, double *logdets, double *grads, ld_info *in
     if (!c || !logdets) return fail(LD_EINVAL, "ctx and logdets must be non-NULL");
     if (!c->is_batch) return fail(LD_EINVAL, "not a batched context");
     const int count = (int)c->subs.size();
-    std::vector<double> out(2 * count);
-    std::vector<int> flags(2 * count);
-    CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
-    CUDA_TRY(cudaGraphLaunch(c->bgraph, c->stream));
-    CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
-    CUDA_TRY(cudaMemcpyAsync(out.data(), c->d_bout.p, sizeof(double) * 2 * count, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(cudaMemcpyAsync(flags.data(), c->d_bint.p, sizeof(int) * 2 * count, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(cudaStreamSynchronize(c->stream));
-    float ms = 0.f;
-    CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    const int nsmall = (int)c->small_idx.size();
+    std::vector<double> out(2 * std::max(nsmall, 1));
+    std::vector<int> flags(2 * std::max(nsmall, 1));
+    const auto t0 = std::chrono::steady_clock::now();
+    // the persistent launch for the small instances first (asynchronous) ...
+    if (nsmall > 0) CUDA_TRY(cudaGraphLaunch(c->bgraph, c->stream));
+    // ... then the large ones, each across the GPU on its own stream
+    std::vector<double> lval(c->large_idx.size()), lseed(c->large_idx.size());
     int iters = 0;
+    int64_t tile_iters = 0, launches = nsmall > 0 ? 3 : 0;
     ld_status st = LD_OK;
-    for (int i = 0; i < count; ++i) {
-        iters = std::max(iters, flags[count + i]);
-        const int f = flags[i];
-        if (f == 0 || st != LD_OK) continue;
+    for (size_t k = 0; k < c->large_idx.size() && st == LD_OK; ++k) {
+        ld_ctx *sc = c->subs[c->large_idx[k]];
+        double o[2] = {0.0, 0.0};
+        ld_info si;
+        std::memset(&si, 0, sizeof si);
+        ld_status s1 = run_solve(sc, 0, sc->ncolours, false, o, &si);
+        if (s1 != LD_OK) {
+            std::string msg = g_err;
+            st = fail(s1, "instance %d: %s", c->large_idx[k], msg.c_str());
+            break;
+        }
+        lval[k] = o[0];
+        lseed[k] = o[1];
+        iters = std::max(iters, (int)si.iters);
+        tile_iters += si.tile_iters;
+        launches += si.gpu_launches;
+    }
+    if (nsmall > 0) {
+        CUDA_TRY(cudaMemcpyAsync(out.data(), c->d_bout.p, sizeof(double) * 2 * nsmall, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(flags.data(), c->d_bint.p, sizeof(int) * 2 * nsmall, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (int k = 0; k < nsmall && st == LD_OK; ++k) {
+        iters = std::max(iters, flags[nsmall + k]);
+        tile_iters += (int64_t)c->subs[c->small_idx[k]]->ntiles * flags[nsmall + k];
+        const int f = flags[k];
+        if (f == 0) continue;
+        const int i = c->small_idx[k];
         if (f == ld::DEV_NOTSPD) st = fail(LD_ENOTSPD, "instance %d: Q is not SPD", i);
         else if (f == -1) st = fail(LD_ENOTCONV, "instance %d: max_iter reached", i);
         else st = fail(LD_ENUMERIC, "instance %d: non-finite CG scalar", i);
@@ -1405,25 +1446,27 @@ ld_status ld_batch_logdet(ld_ctx *c, double *logdets, double *grads, ld_info *in
         info->iters = iters;
         info->tile_width = c->T;
         info->engine = 2;
-        info->ms = ms;
+        info->ms = ms;          // host wall time of the whole batch (both engines)
         info->iter_ms = ms;
-        info->gpu_launches = 3;
+        info->gpu_launches = launches;
         info->bulk_rows = -1;
-        int64_t ti = 0;
-        for (int i = 0; i < count; ++i) ti += (int64_t)c->subs[i]->ntiles * flags[count + i];
-        info->tile_iters = ti;   // upper bound: every tile counted at its instance's iterations
+        info->rel_resid_max = -1.0;
+        info->tile_iters = tile_iters;   // upper bound: every tile counted at its instance's iterations
         info->n_colours = 0;
         for (ld_ctx *sc : c->subs) info->n_colours += sc->ncolours;
     }
     if (st != LD_OK) return st;
-    for (int i = 0; i < count; ++i) {
-        logdets[i] = out[i];
+    auto put = [&](int i, double v, double seed) {
+        logdets[i] = v;
         if (grads) {
             const ld_ctx *sc = c->subs[i];
             const bool projected = (sc->kind == LD_STENCIL_2D5 || sc->kind == LD_STENCIL_3D7) && !sc->has_field;
-            grads[i] = projected ? sc->scale * out[count + i] : std::nan("");
+            grads[i] = projected ? sc->scale * seed : std::nan("");
         }
-    }
+    };
+    for (int k = 0; k < nsmall; ++k) put(c->small_idx[k], out[k], out[nsmall + k]);
+    for (size_t k = 0; k < c->large_idx.size(); ++k) put(c->large_idx[k], lval[k], lseed[k]);
+    (void)count;
     return LD_OK;
 }
 
