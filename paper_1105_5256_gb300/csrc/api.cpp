@@ -1307,7 +1307,7 @@ ld_status ld_batch_create(int count, const ld_matrix *Qs, const int *distances, 
     // Every instance gets a context with a common tile width.  A tile in the persistent
     // launch is one CTA's whole solve, so an instance whose solve would outlast the rest
     // of the batch (CG iterations ~ 8 sqrt(cond), a lattice row of 128 vertices per CTA
-    // step of about a microsecond: more than 0.4 s) runs on the multi-CTA grid engine
+    // step of about a microsecond: more than 0.8 s) runs on the multi-CTA grid engine
     // instead, on its own stream beside the persistent launch.
     ld_options sub = opt;
     sub.keep_x0 = 0;
@@ -1321,7 +1321,7 @@ ld_status ld_batch_create(int count, const ld_matrix *Qs, const int *distances, 
         if (ld_status st = ld_grid_bounds(&Qs[i], &lo, &hi)) return st;
         int32_t dd[3] = {Qs[i].dims[0], Qs[i].dims[1], Qs[i].kind == LD_STENCIL_3D7 ? Qs[i].dims[2] : 1};
         const double est_s = 8.0 * std::sqrt(hi / lo) * ((double)grid_n(dd) / 128.0) * 1.2e-6;
-        const bool large = est_s > 0.4 && grid_n(dd) >= 32768;
+        const bool large = est_s > 0.8 && grid_n(dd) >= 32768;
         ld_options o = sub;
         o.engine = large ? 1 : 2;
         o.cuda_stream = large ? nullptr : c->stream;
