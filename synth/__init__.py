@@ -155,6 +155,18 @@ def random_sparse_spd_pattern(seed: int, n: int, avg_deg: int = 6):
     return rows, cols, w
 
 
+def torus_edges(nx: int, ny: int):
+    """Unit-weight edges (i < j) of the nx x ny periodic 4-neighbour lattice, x fastest;
+    with csr_from_edges(..., kappa2) this is kappa2 I - Lap on the torus as a CSR matrix."""
+    idx = np.arange(nx * ny).reshape(ny, nx)
+    right = np.stack([idx.ravel(), np.roll(idx, -1, axis=1).ravel()], axis=1)
+    down = np.stack([idx.ravel(), np.roll(idx, -1, axis=0).ravel()], axis=1)
+    e = np.concatenate([right, down])
+    e = np.sort(e, axis=1)
+    e = np.unique(e, axis=0)
+    return e[:, 0], e[:, 1], np.ones(len(e))
+
+
 def csr_from_edges(n: int, rows, cols, w, diag_shift) -> tuple:
     """Assemble CSR (int64 rowptr, int32 colidx, f64 val) of L_w + diag(diag_shift).
 

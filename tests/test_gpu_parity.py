@@ -336,3 +336,22 @@ def test_bounded_device_wait_reports_timeout_and_context_stays_usable():
     v, _ = L.ld_logdet(ctx)
     ref = cf.probed_value(om.KIND_2D5, dims, 0.5, True, col, np.log)
     assert abs(v - ref) <= 1e-7 * abs(ref)
+
+
+
+@pytest.mark.parametrize("engine", [1, 2])
+def test_periodic_64_as_csr_matches_closed_form_probing(engine):
+    """The first configuration as given: kappa^2 I - Lap on the 64 x 64 torus as a general
+    CSR matrix, distance 4, 20 shifts, tol 1e-10, FP64, against the spectral oracle."""
+    dims, k2, tol = (64, 64), 0.5, 1e-10
+    rows, cols, w = synth.torus_edges(*dims)
+    rp, ci, vv = synth.csr_from_edges(4096, rows, cols, w, k2)
+    Q = sp.csr_matrix((vv, ci, rp), shape=(4096, 4096))
+    assert abs(Q - om.precision(om.KIND_2D5, dims, k2, periodic=True)).max() == 0
+    col = probing.colour_greedy(Q, 4)
+    ctx = L.ld_create(L.csr_matrix(rp, ci, vv), 4, 20, tol,
+                      L.options(engine=engine, colouring=col, lambda_min=k2, lambda_max=k2 + 8.0))
+    val, info = L.ld_logdet(ctx)
+    s, a = hht.log_nodes(k2, k2 + 8.0, 20)
+    target = spectral_target(om.KIND_2D5, dims, k2, True, col, s, a, per_colour=True)
+    assert abs(val - target.sum()) <= 50 * tol * np.abs(target).sum()
