@@ -106,3 +106,17 @@ def fit(lik: Likelihood, kappa2_0, scale_0, max_iter=40, h=1e-3, gtol=1e-7, max_
             break
     return {"kappa2": float(np.exp(eta[0])), "scale": float(np.exp(eta[1])), "loglik": val,
             "iterations": it, "evaluations": lik.evaluations, "path": path}
+
+
+def fit_schedule(kind, dims, Y, distances=(2, 4, 8), kappa2_0=1.0, scale_0=1.0, periodic=False,
+                 **kw):
+    """Sec. 3's schedule: cheap small-distance colourings for the first iterations, larger
+    ones for the last; each fit starts from the previous estimates.  Returns the list of
+    (distance, fit result)."""
+    out = []
+    k2, s = kappa2_0, scale_0
+    for d in distances:
+        res = fit(Likelihood(kind, dims, Y, d, periodic=periodic), k2, s, **kw)
+        out.append((d, res))
+        k2, s = res["kappa2"], res["scale"]
+    return out

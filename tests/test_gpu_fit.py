@@ -72,3 +72,20 @@ def test_fit_approaches_exact_mle_with_distance():
     print(errs)
     assert errs[1] > errs[4] > errs[8] > errs[16]
     assert errs[16] <= 0.05
+
+
+
+def test_distance_schedule_ends_at_the_large_distance_fit():
+    """Sec. 3's strategy (small colouring distances first, larger at the end) reaches the
+    same estimates as fitting at the final distance from the start, in fewer iterations there."""
+    kind, dims, S = L.LD_STENCIL_2D5, (48, 48), 16
+    n = dims[0] * dims[1]
+    Y = F.sample(kind, dims, 0.3, 2.0, synth.random_probe_block(9, n, S))
+    sched = F.fit_schedule(kind, dims, Y, distances=(2, 8, 16), kappa2_0=0.5, scale_0=1.0)
+    direct = F.fit(F.Likelihood(kind, dims, Y, 16), 0.5, 1.0)
+    last = sched[-1][1]
+    print("schedule:", [(d, round(r["kappa2"], 5), round(r["scale"], 5), r["iterations"]) for d, r in sched],
+          "direct:", round(direct["kappa2"], 5), round(direct["scale"], 5), direct["iterations"])
+    assert abs(last["kappa2"] - direct["kappa2"]) <= 1e-4 * direct["kappa2"]
+    assert abs(last["scale"] - direct["scale"]) <= 1e-4 * direct["scale"]
+    assert last["iterations"] <= direct["iterations"]
