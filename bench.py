@@ -43,7 +43,8 @@ SEED = 2
 METRIC = "log-det(+grad) evals/sec (Matern 1024^2, probing d=2, N=20)"
 UNIT = "evals/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-FP64_FLOPS_PER_VC = 33          # 13-point pass: combine, two difference-form levels, dots
+FP64_FLOPS_PER_VC = 25          # 13-point pass: r, p updates (4), two direct-form 5-point
+                                # levels (5 each) and the scale (1), dot products (10)
 FP64_PEAK_GFLOPS = 1250.0       # measured non-tensor FP64 rate of a GB300
 
 
@@ -403,7 +404,7 @@ def run_ours(args):
     peak, src = peak_hbm()
     traffic = recorded_traffic(T) if args.precision == "mixed" else None
     if args.precision == "fp64":
-        # FP64 issue-bound: 33 flops per vertex-column per pass against the measured
+        # FP64 issue-bound: 25 flops per vertex-column per pass against the measured
         # 1.25 TFLOP/s non-tensor FP64 rate
         flops = FP64_FLOPS_PER_VC * n * T * tile_iters
         roof = {"bound": "alu", "kernel": "fused CG pass (k_stream2d, FP64)",
