@@ -91,7 +91,10 @@ typedef struct {
     int32_t tile_width;       /* probing vectors per tile: 0 = choose automatically */
     int32_t max_iter;         /* CG iteration cap per tile; 0 = 100000 */
     int32_t keep_x0;          /* keep seed solutions Q^{-1} v_c for ld_grad (extra HBM traffic) */
-    double lambda_min;        /* > 0: user lower spectral bound; else library bound */
+    double lambda_min;        /* > 0 (with lambda_max): user spectral interval; else the library's:
+                                 grid kinds exact (Weyl on the lattice eigenvalues), CSR the
+                                 Gershgorin upper bound and half the smallest Ritz value of an
+                                 80-step Lanczos run (LD_ENOTSPD when that is not positive) */
     double lambda_max;        /* > 0: user upper spectral bound; else library bound */
     void *cuda_stream;        /* cudaStream_t to run on; NULL = a stream the context owns */
     const int32_t *colouring; /* optional host colouring (n ints >= 0); NULL = greedy */
@@ -239,6 +242,12 @@ ld_status ld_wait_selftest(int64_t limit_ns);
  * colour: n int32 out.  *n_colours out. */
 ld_status ld_colour_csr(int64_t n, const int64_t *rowptr, const int32_t *colidx, int d,
                         int32_t *colour, int32_t *n_colours);
+
+/* Spectral interval a CSR context uses without user bounds: *lmax = Gershgorin bound of
+ * scale * val, *lmin = half the smallest Ritz value of an 80-step Lanczos run from a fixed
+ * +-1 start vector.  LD_ENOTSPD when the estimate is not positive. */
+ld_status ld_csr_bounds(int64_t n, const int64_t *rowptr, const int32_t *colidx, const double *val,
+                        double scale, double *lmin, double *lmax);
 
 /* Same colouring for a grid kind (lattice-ball search, no CSR needed). */
 ld_status ld_colour_grid(int kind, const int32_t dims[3], int periodic, int d, int32_t *colour,

@@ -103,6 +103,7 @@ def library(build_if_missing: bool = False):
         "ld_colour_grid": ([C.c_int, vp, C.c_int, C.c_int, vp, P(i32)], st),
         "ld_hht_nodes": ([dbl, dbl, C.c_int, vp, vp, P(dbl)], st),
         "ld_grid_bounds": ([P(Matrix), P(dbl), P(dbl)], st),
+        "ld_csr_bounds": ([i64, vp, vp, vp, dbl, P(dbl), P(dbl)], st),
         "ld_batch_create": ([C.c_int, vp, vp, C.c_int, dbl, P(Options), P(vp)], st),
         "ld_batch_logdet": ([vp, vp, vp, vp], st),
         "ld_logdet_static": ([P(Matrix), vp, C.c_int, C.c_int, dbl, C.c_int, vp, P(dbl)], st),
@@ -366,6 +367,17 @@ def ld_hht_nodes(lmin: float, lmax: float, N: int):
     _check(library().ld_hht_nodes(float(lmin), float(lmax), int(N), _ptr(s), _ptr(a),
                                   C.byref(cert)))
     return s[0::2] + 1j * s[1::2], a[0::2] + 1j * a[1::2], cert.value
+
+
+def ld_csr_bounds(rowptr, colidx, val, scale=1.0):
+    """(lmin, lmax) the library uses for a CSR matrix without user bounds (host only)."""
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray(colidx, dtype=np.int32)
+    vv = np.ascontiguousarray(val, dtype=np.float64)
+    lo, hi = C.c_double(), C.c_double()
+    _check(library().ld_csr_bounds(rp.size - 1, _ptr(rp), _ptr(ci), _ptr(vv), float(scale), C.byref(lo),
+                                   C.byref(hi)))
+    return lo.value, hi.value
 
 
 def ld_grid_bounds(matrix):

@@ -89,6 +89,7 @@ struct ld_ctx {
     double tol = 0;
     ld_options opt{};
     bool user_bounds = false;
+    double csr_lmin = 0.0, csr_lmax = 0.0;   // library estimate for CSR without user bounds
     // colouring
     std::vector<int32_t> colour;
     int ncolours = 0;
@@ -267,7 +268,11 @@ ld_status compute_bounds(ld_ctx *c, const double *field) {
         c->lmax = std::max(c->opt.lambda_max, 1.01 * c->opt.lambda_min);
         return LD_OK;
     }
-    if (c->kind == LD_CSR) return fail(LD_EINVAL, "CSR matrices need opt.lambda_min and opt.lambda_max");
+    if (c->kind == LD_CSR) {
+        c->lmin = c->csr_lmin;
+        c->lmax = c->csr_lmax;
+        return LD_OK;
+    }
     double k2min = c->kappa2, k2max = c->kappa2;
     if (c->has_field) {
         k2min = INFINITY;
@@ -715,8 +720,10 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
         if (c->has_mask)
             for (int64_t i = 0; i < c->n && !c->mask_any; ++i) c->mask_any = Q->obs_mask[i] != 0;
     }
-    if (c->kind == LD_CSR && !c->user_bounds)
-        return fail(LD_EINVAL, "CSR matrices need opt.lambda_min and opt.lambda_max > 0");
+    if (c->kind == LD_CSR && !c->user_bounds) {
+        if (ld::csr_bounds(c->n, Q->rowptr, Q->colidx, Q->val, c->scale, &c->csr_lmin, &c->csr_lmax) != 0)
+            return fail(LD_ENOTSPD, "CSR matrix: no positive spectral lower bound (not SPD?)");
+    }
 
     // colouring (Sec. 2.1)
     c->colour.resize(c->n);
@@ -1254,6 +1261,15 @@ ld_status ld_hht_nodes(double lmin, double lmax, int N, double *sigma, double *a
         alpha[2 * l + 1] = a[l].imag();
     }
     if (cert) *cert = ld::hht_certificate(lmin, lmax, N, s.data(), a.data());
+    return LD_OK;
+}
+
+ld_status ld_csr_bounds(int64_t n, const int64_t *rowptr, const int32_t *colidx, const double *val,
+                        double scale, double *lmin, double *lmax) {
+    if (n <= 0 || !rowptr || !colidx || !val || !lmin || !lmax) return fail(LD_EINVAL, "bad arguments");
+    if (!(scale > 0.0)) return fail(LD_EINVAL, "scale must be > 0");
+    if (ld::csr_bounds(n, rowptr, colidx, val, scale, lmin, lmax) != 0)
+        return fail(LD_ENOTSPD, "no positive spectral lower bound (not SPD?)");
     return LD_OK;
 }
 

@@ -9,6 +9,7 @@ import os
 import re
 
 import numpy as np
+import scipy.sparse as sp
 import pytest
 
 import paper_1105_5256_gb300 as L
@@ -130,3 +131,23 @@ def test_invalid_options_rejected_before_any_device_work(lib, kw):
     with pytest.raises(L.LogDetError) as e:
         L.ld_create(L.grid_matrix(om.KIND_2D5, (8, 8), 0.5), 2, 8, 1e-8, L.options(**kw))
     assert e.value.status == L.LD_EINVAL
+
+
+@pytest.mark.parametrize("seed,n,shift", [(21, 600, 0.2), (3, 2000, 0.01), (8, 50, 1.0)])
+def test_csr_bounds_enclose_the_spectrum(lib, seed, n, shift):
+    """Host bound estimate for CSR: Gershgorin above lambda_max; half the smallest Lanczos Ritz
+    value below lambda_min (and within a factor 4 of it), against numpy's eigvalsh."""
+    rows, cols, w = synth.random_sparse_spd_pattern(seed, n)
+    rp, ci, vv = synth.csr_from_edges(n, rows, cols, w, shift)
+    ev = np.linalg.eigvalsh(sp.csr_matrix((vv, ci, rp), shape=(n, n)).toarray())
+    lo, hi = L.ld_csr_bounds(rp, ci, vv, 1.5)
+    assert hi >= 1.5 * ev.max() * (1 - 1e-12)
+    assert 1.5 * ev.min() / 4 <= lo <= 1.5 * ev.min()
+
+
+def test_csr_bounds_reject_indefinite(lib):
+    rp = np.array([0, 1, 2], dtype=np.int64)
+    ci = np.array([0, 1], dtype=np.int32)
+    with pytest.raises(L.LogDetError) as e:
+        L.ld_csr_bounds(rp, ci, np.array([-1.0, -2.0]))
+    assert e.value.status == L.LD_ENOTSPD

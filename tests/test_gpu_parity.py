@@ -355,3 +355,20 @@ def test_periodic_64_as_csr_matches_closed_form_probing(engine):
     s, a = hht.log_nodes(k2, k2 + 8.0, 20)
     target = spectral_target(om.KIND_2D5, dims, k2, True, col, s, a, per_colour=True)
     assert abs(val - target.sum()) <= 50 * tol * np.abs(target).sum()
+
+
+def test_csr_with_library_bounds_matches_exact_probing():
+    """A CSR matrix without user bounds: the library's interval (Gershgorin, Lanczos) must
+    enclose the spectrum, so the result is the exact probed log det to the quadrature and
+    CG accuracy (N = 24 shifts: certificate far below the CG tolerance)."""
+    n = 600
+    rows, cols, w = synth.random_sparse_spd_pattern(21, n)
+    rp, ci, vv = synth.csr_from_edges(n, rows, cols, w, 0.2)
+    Q = sp.csr_matrix((vv, ci, rp), shape=(n, n))
+    col = probing.colour_greedy(Q, 2)
+    ctx = L.ld_create(L.csr_matrix(rp, ci, vv), 2, 24, 1e-11, L.options(colouring=col))
+    val, info = L.ld_logdet(ctx)
+    ev = np.linalg.eigvalsh(Q.toarray())
+    assert info["lambda_min"] <= ev.min() and info["lambda_max"] >= ev.max()
+    ref = mt.probed_dense(Q, col, np.log)
+    assert abs(val - ref) <= 1e-8 * abs(ref)
