@@ -26,10 +26,20 @@
 #include "../../include/logdet.h"
 #include "internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 using ld::Operator;
 using ld::Solve;
 
 namespace {
+
+// NVTX range for profilers (a no-op unless a tool is attached)
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 thread_local std::string g_err = "no error";
 
@@ -407,6 +417,7 @@ void fill_info(const ld_ctx *c, ld_info *info, ld_status st, int iters, float ms
 // One probed solve over colours [cb, ce).  On LD_OK, result[0..1] hold
 // sum of terms and sum of seed projections on the device and in *out.
 ld_status run_solve(ld_ctx *c, int cb, int ce, bool keep_x0, double out[2], ld_info *info) {
+    Range range("ld solve");
     int64_t launches = 0;
     int iters = 0;
     float ms = 0.f;
@@ -726,6 +737,7 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
     }
 
     // colouring (Sec. 2.1)
+    Range create_range("ld create (colouring, tiling, uploads)");
     c->colour.resize(c->n);
     if (opt.colouring) {
         int mx = -1;
@@ -1034,6 +1046,7 @@ ld_status ld_apply(ld_ctx *c, int ncols, const double *x, double *y) {
 // device) pair with the context's shifts: log (the context's weights) or z^{-1/2}
 static ld_status funmv(ld_ctx *c, int ncols, const double *V, double *Y, ld_info *info,
                        const double2 *weight_dev) {
+    Range range("ld vector form");
     if (!c || !V || !Y || ncols < 1) return fail(LD_EINVAL, "bad arguments");
     if (c->is_batch) return fail(LD_EINVAL, "batched context");
     const int T = c->T, N = c->nshift;
@@ -1408,6 +1421,7 @@ ld_status ld_batch_create(int count, const ld_matrix *Qs, const int *distances, 
 }
 
 ld_status ld_batch_logdet(ld_ctx *c, double *logdets, double *grads, ld_info *info) {
+    Range range("ld batch");
     if (!c || !logdets) return fail(LD_EINVAL, "ctx and logdets must be non-NULL");
     if (!c->is_batch) return fail(LD_EINVAL, "not a batched context");
     const int count = (int)c->subs.size();
