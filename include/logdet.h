@@ -243,6 +243,10 @@ ld_status ld_wait_selftest(int64_t limit_ns);
 ld_status ld_colour_csr(int64_t n, const int64_t *rowptr, const int32_t *colidx, int d,
                         int32_t *colour, int32_t *n_colours);
 
+/* Nodes of ld_invsqrt_mv's rational z^{-1/2} on [lmin, lmax]: the log nodes' poles sigma
+ * and weights beta_j = -(2 i h / pi) w'(t_j), interleaved (re, im), N each. */
+ld_status ld_hht_invsqrt_nodes(double lmin, double lmax, int N, double *sigma, double *beta);
+
 /* Spectral interval a CSR context uses without user bounds: *lmax = Gershgorin bound of
  * scale * val, *lmin = half the smallest Ritz value of an 80-step Lanczos run from a fixed
  * +-1 start vector.  LD_ENOTSPD when the estimate is not positive. */

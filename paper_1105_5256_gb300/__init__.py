@@ -104,6 +104,7 @@ def library(build_if_missing: bool = False):
         "ld_hht_nodes": ([dbl, dbl, C.c_int, vp, vp, P(dbl)], st),
         "ld_grid_bounds": ([P(Matrix), P(dbl), P(dbl)], st),
         "ld_csr_bounds": ([i64, vp, vp, vp, dbl, P(dbl), P(dbl)], st),
+        "ld_hht_invsqrt_nodes": ([dbl, dbl, C.c_int, vp, vp], st),
         "ld_batch_create": ([C.c_int, vp, vp, C.c_int, dbl, P(Options), P(vp)], st),
         "ld_batch_logdet": ([vp, vp, vp, vp], st),
         "ld_logdet_static": ([P(Matrix), vp, C.c_int, C.c_int, dbl, C.c_int, vp, P(dbl)], st),
@@ -367,6 +368,13 @@ def ld_hht_nodes(lmin: float, lmax: float, N: int):
     _check(library().ld_hht_nodes(float(lmin), float(lmax), int(N), _ptr(s), _ptr(a),
                                   C.byref(cert)))
     return s[0::2] + 1j * s[1::2], a[0::2] + 1j * a[1::2], cert.value
+
+
+def ld_hht_invsqrt_nodes(lmin: float, lmax: float, N: int):
+    s = np.zeros(2 * N)
+    b = np.zeros(2 * N)
+    _check(library().ld_hht_invsqrt_nodes(float(lmin), float(lmax), int(N), _ptr(s), _ptr(b)))
+    return s[0::2] + 1j * s[1::2], b[0::2] + 1j * b[1::2]
 
 
 def ld_csr_bounds(rowptr, colidx, val, scale=1.0):

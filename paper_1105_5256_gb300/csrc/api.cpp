@@ -1277,6 +1277,20 @@ ld_status ld_hht_nodes(double lmin, double lmax, int N, double *sigma, double *a
     return LD_OK;
 }
 
+ld_status ld_hht_invsqrt_nodes(double lmin, double lmax, int N, double *sigma, double *beta) {
+    if (N < 1 || N > 256 || !sigma || !beta) return fail(LD_EINVAL, "bad arguments");
+    std::vector<std::complex<double>> s(N), b(N);
+    if (ld::hht_invsqrt_nodes(lmin, lmax, N, s.data(), b.data()) != 0)
+        return fail(LD_EINVAL, "need 0 < lmin < lmax");
+    for (int l = 0; l < N; ++l) {
+        sigma[2 * l] = s[l].real();
+        sigma[2 * l + 1] = s[l].imag();
+        beta[2 * l] = b[l].real();
+        beta[2 * l + 1] = b[l].imag();
+    }
+    return LD_OK;
+}
+
 ld_status ld_csr_bounds(int64_t n, const int64_t *rowptr, const int32_t *colidx, const double *val,
                         double scale, double *lmin, double *lmax) {
     if (n <= 0 || !rowptr || !colidx || !val || !lmin || !lmax) return fail(LD_EINVAL, "bad arguments");

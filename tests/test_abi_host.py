@@ -85,6 +85,14 @@ def test_nodes_match_oracle(lib, m, M, N):
     assert abs(cert - co) <= 1e-12 + 1e-6 * co
 
 
+@pytest.mark.parametrize("m,M,N", [(0.5, 8.5, 20), (1e-4, 64.2, 24), (3.0, 3e6, 40)])
+def test_invsqrt_nodes_match_oracle(lib, m, M, N):
+    s, b = L.ld_hht_invsqrt_nodes(m, M, N)
+    so, bo = hht.invsqrt_nodes(m, M, N)
+    assert np.abs(s - so).max() <= 1e-12 * np.abs(so).max()
+    assert np.abs(b - bo).max() <= 1e-12 * np.abs(bo).max()
+
+
 def test_node_errors(lib):
     with pytest.raises(L.LogDetError):
         L.ld_hht_nodes(-1.0, 2.0, 8)
