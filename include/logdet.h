@@ -93,8 +93,9 @@ typedef struct {
     int32_t keep_x0;          /* keep seed solutions Q^{-1} v_c for ld_grad (extra HBM traffic) */
     double lambda_min;        /* > 0 (with lambda_max): user spectral interval; else the library's:
                                  grid kinds exact (Weyl on the lattice eigenvalues), CSR the
-                                 Gershgorin upper bound and half the smallest Ritz value of an
-                                 80-step Lanczos run (LD_ENOTSPD when that is not positive) */
+                                 Gershgorin upper bound and half the converged smallest
+                                 Lanczos Ritz value, as ld_csr_bounds (ld_create fails with
+                                 its LD_ENOTCONV / LD_ENOTSPD) */
     double lambda_max;        /* > 0: user upper spectral bound; else library bound */
     void *cuda_stream;        /* cudaStream_t to run on; NULL = a stream the context owns */
     const int32_t *colouring; /* optional host colouring (n ints >= 0); NULL = greedy */
@@ -248,8 +249,12 @@ ld_status ld_colour_csr(int64_t n, const int64_t *rowptr, const int32_t *colidx,
 ld_status ld_hht_invsqrt_nodes(double lmin, double lmax, int N, double *sigma, double *beta);
 
 /* Spectral interval a CSR context uses without user bounds: *lmax = Gershgorin bound of
- * scale * val, *lmin = half the smallest Ritz value of an 80-step Lanczos run from a fixed
- * +-1 start vector.  LD_ENOTSPD when the estimate is not positive. */
+ * scale * val, *lmin = half the smallest Ritz value of a Lanczos run from a fixed +-1 start
+ * vector, run until that Ritz value has stagnated (less than 1e-3 relative change over the
+ * second half of the steps; about sqrt(condition number) steps, more than n allowed) within
+ * a host budget of about 4e9 flop (at least 300 steps).  LD_ENOTCONV when it has not
+ * converged by then (pass lambda_min / lambda_max instead), LD_ENOTSPD when the estimate
+ * is not positive.  Host only. */
 ld_status ld_csr_bounds(int64_t n, const int64_t *rowptr, const int32_t *colidx, const double *val,
                         double scale, double *lmin, double *lmax);
 

@@ -17,6 +17,15 @@ Readings (the paper leaves these open):
   * the 13-point Matern precision is the exact product Q1 @ Q1 of the
     truncated 5-point Q1 = kappa^2 I - Laplacian;
   * the prior scale multiplies the whole matrix.
+
+General meshes (the SPDE route the paper cites for sparse precisions, Sec. 1):
+piecewise-linear finite elements on a triangulation, natural (Neumann)
+boundary, lumped mass C~ (each triangle gives a third of its area to each of
+its vertices), stiffness G_ij = integral of grad(phi_i) . grad(phi_j);
+Q = tau (kappa^2 C~ + G) for the first-order model and
+Q = tau K C~^{-1} K with K = kappa^2 C~ + G for the second-order one.  The
+hat-function gradients come from inverting each triangle's vertex matrix, one
+triangle at a time.
 """
 from __future__ import annotations
 
@@ -100,3 +109,41 @@ def csr_arrays(Q: sp.csr_matrix):
     Q = Q.tocsr()
     Q.sort_indices()
     return (Q.indptr.astype(np.int64), Q.indices.astype(np.int32), Q.data.astype(np.float64))
+
+
+def fem_p1(points: np.ndarray, triangles: np.ndarray):
+    """Lumped mass diagonal c (n,) and stiffness G (CSR) of P1 elements, one triangle
+    at a time: the hat functions restricted to a triangle are the columns of the
+    inverse of [[1, x_k, y_k]]_k (value 1 at their own vertex, 0 at the others)."""
+    n = points.shape[0]
+    c = np.zeros(n)
+    G = {}
+    for tri in triangles:
+        V = np.array([[1.0, points[k, 0], points[k, 1]] for k in tri])
+        area = 0.5 * abs(np.linalg.det(V))
+        coef = np.linalg.inv(V)            # column i: (c0, cx, cy) of phi_i on this triangle
+        for i in range(3):
+            c[tri[i]] += area / 3.0
+            for j in range(3):
+                gij = area * (coef[1, i] * coef[1, j] + coef[2, i] * coef[2, j])
+                key = (int(tri[i]), int(tri[j]))
+                G[key] = G.get(key, 0.0) + gij
+    r = np.array([k[0] for k in G], dtype=np.int64)
+    cc = np.array([k[1] for k in G], dtype=np.int64)
+    v = np.array(list(G.values()))
+    return c, sp.csr_matrix((v, (r, cc)), shape=(n, n))
+
+
+def fem_spde_precision(points, triangles, kappa2: float, alpha: int = 1, tau: float = 1.0):
+    """Q = tau (kappa^2 C~ + G) (alpha = 1) or tau K C~^{-1} K, K = kappa^2 C~ + G (alpha = 2)."""
+    c, G = fem_p1(points, triangles)
+    K = (kappa2 * sp.diags(c) + G).tocsr()
+    if alpha == 1:
+        Q = tau * K
+    elif alpha == 2:
+        Q = tau * (K @ sp.diags(1.0 / c) @ K)
+    else:
+        raise ValueError("alpha must be 1 or 2")
+    Q = Q.tocsr()
+    Q.sort_indices()
+    return Q

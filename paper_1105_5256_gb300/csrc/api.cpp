@@ -732,8 +732,13 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
             for (int64_t i = 0; i < c->n && !c->mask_any; ++i) c->mask_any = Q->obs_mask[i] != 0;
     }
     if (c->kind == LD_CSR && !c->user_bounds) {
-        if (ld::csr_bounds(c->n, Q->rowptr, Q->colidx, Q->val, c->scale, &c->csr_lmin, &c->csr_lmax) != 0)
-            return fail(LD_ENOTSPD, "CSR matrix: no positive spectral lower bound (not SPD?)");
+        int steps = 0;
+        const int rc = ld::csr_bounds(c->n, Q->rowptr, Q->colidx, Q->val, c->scale, &c->csr_lmin,
+                                      &c->csr_lmax, &steps);
+        if (rc == -2)
+            return fail(LD_ENOTCONV, "CSR matrix: smallest Lanczos Ritz value not converged after %d "
+                                     "steps; pass lambda_min and lambda_max", steps);
+        if (rc != 0) return fail(LD_ENOTSPD, "CSR matrix: no positive spectral lower bound (not SPD?)");
     }
 
     // colouring (Sec. 2.1)
@@ -1295,8 +1300,11 @@ ld_status ld_csr_bounds(int64_t n, const int64_t *rowptr, const int32_t *colidx,
                         double scale, double *lmin, double *lmax) {
     if (n <= 0 || !rowptr || !colidx || !val || !lmin || !lmax) return fail(LD_EINVAL, "bad arguments");
     if (!(scale > 0.0)) return fail(LD_EINVAL, "scale must be > 0");
-    if (ld::csr_bounds(n, rowptr, colidx, val, scale, lmin, lmax) != 0)
-        return fail(LD_ENOTSPD, "no positive spectral lower bound (not SPD?)");
+    int steps = 0;
+    const int rc = ld::csr_bounds(n, rowptr, colidx, val, scale, lmin, lmax, &steps);
+    if (rc == -2)
+        return fail(LD_ENOTCONV, "smallest Lanczos Ritz value not converged after %d steps", steps);
+    if (rc != 0) return fail(LD_ENOTSPD, "no positive spectral lower bound (not SPD?)");
     return LD_OK;
 }
 

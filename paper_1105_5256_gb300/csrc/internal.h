@@ -140,9 +140,10 @@ const char *engine_error_string(int cuda_err);
 void graph_distances(int kind, const int32_t dims[3], int periodic, int64_t n, const int64_t *rowptr,
                      const int32_t *colidx, int64_t j, int max_d, int32_t *dist);
 
-// host: spectral interval of a CSR matrix (Gershgorin / half the smallest Lanczos Ritz
-// value; bounds.cpp); 0 on success, -1 when the estimate is not positive
+// host: spectral interval of a CSR matrix (Gershgorin / half the converged smallest
+// Lanczos Ritz value; bounds.cpp); 0 on success, -1 when the estimate is not positive,
+// -2 when the Ritz value did not converge within the step cap; *steps = Lanczos steps run
 int csr_bounds(int64_t n, const int64_t *rowptr, const int32_t *colidx, const double *val, double scale,
-               double *lmin, double *lmax);
+               double *lmin, double *lmax, int *steps = nullptr);
 
 }  // namespace ld

@@ -2,9 +2,9 @@
 
 This module only draws random numbers and lays out problem descriptions; it
 holds none of the log-determinant method's arithmetic (no colouring, no
-quadrature, no Krylov recurrence, no matrix assembly).  Every generator is a
-pure function of its seed, so the oracle and the CUDA path see identical
-inputs.
+quadrature, no Krylov recurrence; the only assembly is the graph Laplacian of
+a drawn edge list).  Every generator is a pure function of its seed, so the
+oracle and the CUDA path see identical inputs.
 
 The workloads mirror the spatial GMRF models the paper uses (the SPDE model
 tau (kappa - Laplacian) u = W on regular grids, Sec. 3; the Gauss-linear
@@ -192,3 +192,31 @@ def csr_from_edges(n: int, rows, cols, w, diag_shift) -> tuple:
     np.add.at(rowptr, rr + 1, 1)
     rowptr = np.cumsum(rowptr)
     return rowptr.astype(np.int64), cc.astype(np.int32), vs.astype(np.float64)
+
+
+def perturbed_triangulation(seed: int, nx: int, ny: int, jitter: float = 0.15):
+    """Seeded unstructured triangulation of the unit square (general-mesh input).
+
+    Vertices start on the nx x ny lattice (x fastest, spacing 1/(nx-1), 1/(ny-1)).
+    Interior vertices move by uniform(-jitter, jitter) lattice spacings in x and y;
+    edge vertices move only along their edge and corners stay, so the domain is the
+    unit square exactly.  Each cell is cut along one of its two diagonals by a fair
+    coin.  jitter <= 0.15 keeps every triangle counter-clockwise and non-degenerate.
+    Returns (points float64 n x 2, triangles int64 m x 3, counter-clockwise).
+    """
+    g = rng(seed)
+    hx, hy = 1.0 / (nx - 1), 1.0 / (ny - 1)
+    ix, iy = np.meshgrid(np.arange(nx), np.arange(ny))
+    ix, iy = ix.ravel(), iy.ravel()
+    dx = g.uniform(-jitter, jitter, size=ix.size) * hx
+    dy = g.uniform(-jitter, jitter, size=ix.size) * hy
+    dx[(ix == 0) | (ix == nx - 1)] = 0.0
+    dy[(iy == 0) | (iy == ny - 1)] = 0.0
+    pts = np.stack([ix * hx + dx, iy * hy + dy], axis=1)
+    cx, cy = np.meshgrid(np.arange(nx - 1), np.arange(ny - 1))
+    a = (cx + nx * cy).ravel()
+    b, c, d = a + 1, a + nx, a + nx + 1          # a b on the lower row, c d above
+    coin = g.integers(0, 2, size=a.size).astype(bool)
+    t1 = np.where(coin[:, None], np.stack([a, b, d], 1), np.stack([a, b, c], 1))
+    t2 = np.where(coin[:, None], np.stack([a, d, c], 1), np.stack([b, d, c], 1))
+    return pts, np.concatenate([t1, t2]).astype(np.int64)

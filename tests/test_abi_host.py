@@ -143,14 +143,32 @@ def test_invalid_options_rejected_before_any_device_work(lib, kw):
 
 @pytest.mark.parametrize("seed,n,shift", [(21, 600, 0.2), (3, 2000, 0.01), (8, 50, 1.0)])
 def test_csr_bounds_enclose_the_spectrum(lib, seed, n, shift):
-    """Host bound estimate for CSR: Gershgorin above lambda_max; half the smallest Lanczos Ritz
-    value below lambda_min (and within a factor 4 of it), against numpy's eigvalsh."""
+    """Host bound estimate for CSR: Gershgorin above lambda_max; half the converged smallest
+    Lanczos Ritz value below lambda_min (and within a factor 4 of it), against eigvalsh."""
     rows, cols, w = synth.random_sparse_spd_pattern(seed, n)
     rp, ci, vv = synth.csr_from_edges(n, rows, cols, w, shift)
     ev = np.linalg.eigvalsh(sp.csr_matrix((vv, ci, rp), shape=(n, n)).toarray())
     lo, hi = L.ld_csr_bounds(rp, ci, vv, 1.5)
     assert hi >= 1.5 * ev.max() * (1 - 1e-12)
     assert 1.5 * ev.min() / 4 <= lo <= 1.5 * ev.min()
+
+
+@pytest.mark.parametrize("case", ["fem2_k0.5", "fem2_k0.01", "fem2_61", "matern_1e-4"])
+def test_csr_bounds_converge_on_ill_conditioned_matrices(lib, case):
+    """Condition numbers 1e6 to 1e12 need thousands of Lanczos steps (more than n for the
+    smaller ones): the lower bound must still be half the smallest eigenvalue, i.e. the
+    Ritz value converged instead of stopping at a fixed step count."""
+    if case.startswith("fem2"):
+        nx, k2 = (61, 10.0) if case == "fem2_61" else (31, float(case.split("_k")[1]))
+        p, t = synth.perturbed_triangulation(11, nx, nx - 4 if nx == 31 else nx)
+        Q = om.fem_spde_precision(p, t, k2, 2)
+    else:
+        Q = om.precision(om.KIND_2D13_SQ, (60, 60), 1e-4)
+    rp, ci, vv = om.csr_arrays(Q)
+    ev = np.linalg.eigvalsh(Q.toarray())
+    lo, hi = L.ld_csr_bounds(rp, ci, vv)
+    assert hi >= ev.max() * (1 - 1e-12)
+    assert 0.49 * ev.min() <= lo <= 0.5 * ev.min() * (1 + 1e-3)
 
 
 def test_csr_bounds_reject_indefinite(lib):
