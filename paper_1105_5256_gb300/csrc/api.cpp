@@ -225,6 +225,8 @@ ld_status validate_matrix(const ld_matrix *Q) {
         if (d < nd && Q->dims[d] < 1) return fail(LD_EINVAL, "dims[%d] must be >= 1", d);
         if (d >= nd && Q->dims[d] != 1 && Q->dims[d] != 0) return fail(LD_EINVAL, "dims[%d] must be 1 for this kind", d);
     }
+    if ((double)Q->dims[0] * (double)Q->dims[1] * (double)(nd == 3 ? Q->dims[2] : 1) > 4.0e12)
+        return fail(LD_EINVAL, "grid has more than 4e12 vertices");
     if (!std::isfinite(Q->kappa2) || Q->kappa2 < 0.0) return fail(LD_EINVAL, "kappa2 must be finite and >= 0");
     if (Q->kind == LD_STENCIL_2D13_SQ && (Q->kappa2_field || (Q->obs_mask && Q->tau != 0.0)))
         return fail(LD_EUNSUPPORTED, "13-point Matern kind takes a scalar kappa2 and no observation term");
