@@ -171,6 +171,21 @@ def test_csr_bounds_converge_on_ill_conditioned_matrices(lib, case):
     assert 0.49 * ev.min() <= lo <= 0.5 * ev.min() * (1 + 1e-3)
 
 
+def test_csr_bounds_unconverged_is_an_error_not_a_guess(lib):
+    """A 1D chain with kappa^2 = 1e-8 (condition number about 4e8, 2e4 Lanczos steps) and
+    200k vertices: the host step budget runs out first, so the bound fails with LD_ENOTCONV
+    and ld_create asks for user bounds instead of using an unconverged estimate."""
+    n = 200_000
+    rows = np.arange(1, n, dtype=np.int64)
+    rp, ci, vv = synth.csr_from_edges(n, rows, rows - 1, np.ones(n - 1), 1e-8)
+    with pytest.raises(L.LogDetError) as e:
+        L.ld_csr_bounds(rp, ci, vv)
+    assert e.value.status == L.LD_ENOTCONV
+    with pytest.raises(L.LogDetError) as e:
+        L.ld_create(L.csr_matrix(rp, ci, vv), 1, 8, 1e-6)
+    assert e.value.status == L.LD_ENOTCONV and "lambda_min" in L.ld_last_error()
+
+
 def test_csr_bounds_reject_indefinite(lib):
     rp = np.array([0, 1, 2], dtype=np.int64)
     ci = np.array([0, 1], dtype=np.int32)
