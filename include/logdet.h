@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define LD_ABI_VERSION 3
+#define LD_ABI_VERSION 4
 
 typedef struct ld_ctx ld_ctx;
 
@@ -49,7 +49,8 @@ typedef enum {
     LD_ENOTCONV = 5,      /* max_iter reached before every shifted system converged */
     LD_ENUMERIC = 6,      /* NaN/Inf in the CG scalars */
     LD_ETIMEOUT = 7,      /* a bounded device wait ran out */
-    LD_EUNSUPPORTED = 8   /* combination not implemented */
+    LD_EUNSUPPORTED = 8,  /* combination not implemented */
+    LD_ECALLBACK = 9      /* a caller-supplied matvec callback returned nonzero */
 } ld_status;
 
 typedef enum { LD_FP64 = 0, LD_MIXED = 1 } ld_precision;
@@ -61,7 +62,8 @@ typedef enum {
     LD_CSR = 0,            /* general symmetric CSR matrix */
     LD_STENCIL_2D5 = 1,    /* scale*(diag(kappa2) - Lap_5pt + tau*diag(mask)) on nx x ny */
     LD_STENCIL_2D13_SQ = 2,/* scale*(kappa2 I - Lap_5pt)^2 (13-point Matern alpha=2) */
-    LD_STENCIL_3D7 = 3     /* scale*(diag(kappa2) - Lap_7pt + tau*diag(mask)) on nx x ny x nz */
+    LD_STENCIL_3D7 = 3,    /* scale*(diag(kappa2) - Lap_7pt + tau*diag(mask)) on nx x ny x nz */
+    LD_MATFREE = 4         /* kind of an ld_create_matfree context (not valid in ld_matrix) */
 } ld_kind;
 
 /* Hyperparameter ids for gradients: dQ/d eta. */
@@ -117,7 +119,7 @@ typedef struct {
     int32_t n_shifts;         /* quadrature nodes N */
     int32_t iters;            /* CG iterations (maximum over tiles) */
     int32_t tile_width;
-    int32_t engine;
+    int32_t engine;           /* 1 multi-CTA grid engine, 2 one-CTA-per-tile, 3 matrix-free driver */
     double lambda_min, lambda_max; /* interval enclosing the spectrum used for the nodes */
     double quad_cert;         /* max |f_N(lambda) - log lambda| on [lambda_min, lambda_max] */
     double ms;                /* device time of the solve (CUDA events) */
@@ -153,6 +155,39 @@ ld_status ld_default_options(ld_options *opt);
  * Errors: LD_EINVAL, LD_EUNSUPPORTED, LD_ENOMEM, LD_ECUDA. */
 ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, double tol,
                     const ld_options *opt, ld_ctx **out);
+
+/* Matrix-free operator (Sec. 1: the method needs Q only through products Q v).
+ * Enqueue W = Q P on `stream` (a cudaStream_t; or finish the product before returning).
+ * P and W are device arrays of n x ncols doubles owned by the library, row-major (entry
+ * (i, c) at i * ncols + c; column c is the probing vector of colour colour_begin + c of
+ * the solve); P is read-only, every entry of W must be written.  Called once per CG
+ * iteration from the thread that called ld_logdet / ld_logdet_partial.  Return 0 on
+ * success; anything else stops the solve with LD_ECALLBACK. */
+typedef int (*ld_matvec_fn)(void *user, int64_t n, int32_t ncols, const double *P, double *W,
+                            void *stream);
+
+/* Create a context for an SPD operator given only by matvec (Sec. 2.1 method without a
+ * matrix):
+ *   n              dimension, 1 <= n <= 2^40.
+ *   matvec, user   the product callback and its opaque argument (borrowed for the
+ *                  context's lifetime).
+ *   colouring      n colours in [0, n) (host, copied): the probing vectors are the
+ *                  indicators of its classes; a distance-d colouring of the operator's
+ *                  graph (ld_colour_csr on its pattern) gives the method's estimate.
+ *   lambda_min, lambda_max   0 < lambda_min < lambda_max enclosing the spectrum (the
+ *                  library cannot estimate them without the matrix).
+ *   n_shifts, tol  as ld_create.
+ *   opt            NULL = defaults; cuda_stream and max_iter are used, precision must be
+ *                  LD_FP64 (LD_EUNSUPPORTED otherwise), the rest is ignored.
+ * The solve runs plain CG with the projected multi-shift recurrences in the library's
+ * kernels, two reductions per iteration, n x C FP64 vectors r, p, w on the device.  Only
+ * ld_logdet, ld_logdet_partial, ld_column_terms (seed projections NaN), ld_get_colouring,
+ * ld_get_nodes and ld_destroy accept the context; the rest return LD_EUNSUPPORTED.
+ * Errors: LD_EINVAL (checked before any device call), LD_EUNSUPPORTED, LD_ENOMEM,
+ * LD_ECUDA; ld_logdet adds LD_ECALLBACK, LD_ENOTSPD, LD_ENOTCONV, LD_ENUMERIC. */
+ld_status ld_create_matfree(int64_t n, ld_matvec_fn matvec, void *user, const int32_t *colouring,
+                            double lambda_min, double lambda_max, int n_shifts, double tol,
+                            const ld_options *opt, ld_ctx **out);
 
 /* Replace kappa2 (or its field multiplier), tau and scale, keeping the pattern and
  * colouring (Sec. 3: colourings are computed once and stored).  Spectral bounds and

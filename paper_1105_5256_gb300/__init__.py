@@ -23,13 +23,14 @@ import numpy as np
 from ._build import OUT as _LIB_PATH
 
 LD_OK, LD_EINVAL, LD_ENOMEM, LD_ECUDA, LD_ENOTSPD, LD_ENOTCONV, LD_ENUMERIC, LD_ETIMEOUT, \
-    LD_EUNSUPPORTED = range(9)
+    LD_EUNSUPPORTED, LD_ECALLBACK = range(10)
 LD_FP64, LD_MIXED = 0, 1
-LD_CSR, LD_STENCIL_2D5, LD_STENCIL_2D13_SQ, LD_STENCIL_3D7 = 0, 1, 2, 3
+LD_CSR, LD_STENCIL_2D5, LD_STENCIL_2D13_SQ, LD_STENCIL_3D7, LD_MATFREE = 0, 1, 2, 3, 4
 LD_P_KAPPA2, LD_P_TAU, LD_P_SCALE = 0, 1, 2
 
 STATUS_NAMES = {0: "LD_OK", 1: "LD_EINVAL", 2: "LD_ENOMEM", 3: "LD_ECUDA", 4: "LD_ENOTSPD",
-                5: "LD_ENOTCONV", 6: "LD_ENUMERIC", 7: "LD_ETIMEOUT", 8: "LD_EUNSUPPORTED"}
+                5: "LD_ENOTCONV", 6: "LD_ENUMERIC", 7: "LD_ETIMEOUT", 8: "LD_EUNSUPPORTED",
+                9: "LD_ECALLBACK"}
 
 
 class LogDetError(RuntimeError):
@@ -66,6 +67,9 @@ class Info(C.Structure):
 
 _lib = None
 
+# ld_matvec_fn: int (*)(void *user, int64_t n, int32_t ncols, const double *P, double *W, void *stream)
+MATVEC_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p)
+
 
 def library(build_if_missing: bool = False):
     """Load liblogdet.so (raises if it is missing: there is no fallback path)."""
@@ -85,6 +89,7 @@ def library(build_if_missing: bool = False):
         "ld_abi_version": ([], C.c_int),
         "ld_default_options": ([P(Options)], st),
         "ld_create": ([P(Matrix), C.c_int, C.c_int, dbl, P(Options), P(vp)], st),
+        "ld_create_matfree": ([i64, MATVEC_FN, vp, vp, dbl, dbl, C.c_int, dbl, P(Options), P(vp)], st),
         "ld_set_params": ([vp, dbl, dbl, dbl], st),
         "ld_logdet": ([vp, P(dbl), P(Info)], st),
         "ld_logdet_grad": ([vp, C.c_int, vp, P(dbl), vp, P(Info)], st),
@@ -216,6 +221,49 @@ def ld_create(matrix, colouring_distance: int, n_shifts: int, tol: float, opts: 
                                C.byref(o), C.byref(h)))
     n = int(m.n) if m.kind == LD_CSR else int(np.prod([max(1, x) for x in m.dims]))
     return Context(h, n, keep)
+
+
+class _DeviceRows:
+    """__cuda_array_interface__ of a library-owned n x ncols float64 device array."""
+
+    def __init__(self, ptr, n, ncols):
+        self.__cuda_array_interface__ = {"shape": (int(n), int(ncols)), "typestr": "<f8",
+                                         "data": (int(ptr), False), "version": 2, "strides": None}
+
+
+def ld_create_matfree(n: int, matvec, colouring, lambda_min: float, lambda_max: float, n_shifts: int,
+                      tol: float, opts: Options = None):
+    """Context for an SPD operator known only through matvec(P, W): P and W are torch
+    float64 CUDA tensors (n x ncols views of the library's device buffers, row-major) and
+    matvec must write W = Q P; it runs with the library's stream as torch's current stream.
+    An exception inside matvec stops the solve with LD_ECALLBACK (the exception is kept in
+    ctx.matvec_error)."""
+    col = np.ascontiguousarray(colouring, dtype=np.int32)
+    ctx_box = {}
+
+    def call(user, n_, ncols, P, W, stream):
+        try:
+            import torch
+            Pt = torch.as_tensor(_DeviceRows(P, n_, ncols), device="cuda")
+            Wt = torch.as_tensor(_DeviceRows(W, n_, ncols), device="cuda")
+            with torch.cuda.stream(torch.cuda.ExternalStream(int(stream))):
+                matvec(Pt, Wt)
+            return 0
+        except BaseException as e:   # noqa: BLE001 -- reported through LD_ECALLBACK
+            if "ctx" in ctx_box:
+                ctx_box["ctx"].matvec_error = e
+            return 1
+
+    fn = MATVEC_FN(call) if matvec is not None else MATVEC_FN()
+    h = C.c_void_p()
+    o = opts if opts is not None else options()
+    _check(library().ld_create_matfree(int(n), fn, None, _ptr(col) if col.size else None,
+                                       float(lambda_min), float(lambda_max), int(n_shifts),
+                                       float(tol), C.byref(o), C.byref(h)))
+    ctx = Context(h, int(n), [fn, col, o])
+    ctx.matvec_error = None
+    ctx_box["ctx"] = ctx
+    return ctx
 
 
 def ld_set_params(ctx: Context, kappa2: float, tau: float = 0.0, scale: float = 1.0):

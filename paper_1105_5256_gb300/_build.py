@@ -17,7 +17,7 @@ OUT = os.path.join(PKG, "liblogdet.so")
 BUILD = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["engine.cu", "engine_iter_f32.cu", "engine_iter_f64.cu", "static_scratch.cu"]
+CU_SOURCES = ["engine.cu", "engine_iter_f32.cu", "engine_iter_f64.cu", "static_scratch.cu", "matfree.cu"]
 CXX_SOURCES = ["api.cpp", "bounds.cpp", "colouring.cpp", "hht.cpp"]
 HEADERS = ["internal.h", "engine_device.cuh", "engine_iter.cuh"]
 

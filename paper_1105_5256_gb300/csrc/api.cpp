@@ -144,8 +144,12 @@ struct ld_ctx {
     // batch: instances in the persistent launch (small) and on the multi-CTA engine (large)
     std::vector<int> small_idx, large_idx;
     cudaGraphExec_t bgraph = nullptr;
+    // matrix-free operator (ld_create_matfree): the caller's W = Q P drives the solve
+    ld::Matfree *mf = nullptr;
+    std::vector<double> mf_terms;
 
     ~ld_ctx() {
+        if (mf) ld::matfree_destroy(mf);
         if (bgraph) cudaGraphExecDestroy(bgraph);
         for (ld_ctx *c : subs) delete c;
         if (graph) cudaGraphExecDestroy(graph);
@@ -413,7 +417,40 @@ void fill_info(const ld_ctx *c, ld_info *info, ld_status st, int iters, float ms
     info->ms = ms;
     info->gpu_launches = launches;
     const bool lattice2d = c->s.op.kind == ld::KIND_2D5 || c->s.op.kind == ld::KIND_2D13_SQ;
-    info->bulk_rows = c->engine == 1 && lattice2d ? c->s.bulk : -1;
+    info->bulk_rows = c->engine == 1 && lattice2d && !c->mf ? c->s.bulk : -1;
+    info->reliable_updates = 0;
+    info->rel_resid_max = -1.0;
+}
+
+// matrix-free contexts support ld_logdet, ld_logdet_partial and the getters only
+#define REJECT_MATFREE(c)                                                                     \
+    do {                                                                                      \
+        if ((c)->mf) return fail(LD_EUNSUPPORTED, "matrix-free context: ld_logdet and "       \
+                                                  "ld_logdet_partial only");                  \
+    } while (0)
+
+// matrix-free solve over colours [cb, ce); out[0] = sum of the terms
+ld_status run_matfree(ld_ctx *c, int cb, int ce, double out[2], ld_info *info) {
+    Range range("ld matrix-free solve");
+    ld::MatfreeStats ms{};
+    std::vector<double> terms(std::max(ce - cb, 0));
+    const int max_iter = c->opt.max_iter > 0 ? c->opt.max_iter : 100000;
+    const ld_status st = (ld_status)ld::matfree_solve(c->mf, cb, ce, c->sigma.data(), c->alpha.data(),
+                                                      c->tol, max_iter, c->stream, terms.data(), &ms);
+    fill_info(c, info, st, ms.iters, ms.ms, ms.launches, ms.ms, ms.column_iters);
+    if (st != LD_OK) return st;
+    double sum = 0.0;
+    for (int k = 0; k < ce - cb; ++k) {
+        c->mf_terms[cb + k] = terms[k];
+        sum += terms[k];
+    }
+    if (!std::isfinite(sum)) return fail(LD_ENUMERIC, "non-finite log det");
+    out[0] = sum;
+    out[1] = 0.0;
+    c->solved = true;
+    c->last_cb = cb;
+    c->last_ce = ce;
+    return LD_OK;
 }
 
 // One probed solve over colours [cb, ce).  On LD_OK, result[0..1] hold
@@ -897,9 +934,70 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
     return LD_OK;
 }
 
+ld_status ld_create_matfree(int64_t n, ld_matvec_fn matvec, void *user, const int32_t *colouring,
+                            double lambda_min, double lambda_max, int n_shifts, double tol,
+                            const ld_options *opt_in, ld_ctx **out) {
+    Range range("ld create matrix-free");
+    if (!out) return fail(LD_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!matvec || !colouring) return fail(LD_EINVAL, "matvec and colouring must be non-NULL");
+    if (n <= 0 || n > ((int64_t)1 << 40)) return fail(LD_EINVAL, "n must be in [1, 2^40]");
+    if (n_shifts < 1 || n_shifts > 256) return fail(LD_EINVAL, "n_shifts must be in [1, 256]");
+    if (!(tol > 0.0 && tol < 1.0)) return fail(LD_EINVAL, "tol must be in (0, 1)");
+    if (!(lambda_min > 0.0) || !(lambda_max > lambda_min) || !std::isfinite(lambda_max))
+        return fail(LD_EINVAL, "need 0 < lambda_min < lambda_max (finite)");
+    ld_options opt;
+    ld_default_options(&opt);
+    if (opt_in) opt = *opt_in;
+    if (opt.precision != LD_FP64) return fail(LD_EUNSUPPORTED, "matrix-free contexts run in FP64");
+    if (opt.max_iter < 0) return fail(LD_EINVAL, "max_iter must be >= 0");
+    int mx = -1;
+    for (int64_t i = 0; i < n; ++i) {
+        if (colouring[i] < 0 || colouring[i] >= n) return fail(LD_EINVAL, "colour at %lld outside [0, n)", (long long)i);
+        mx = std::max(mx, (int)colouring[i]);
+    }
+    ld_ctx *c = new (std::nothrow) ld_ctx();
+    if (!c) return fail(LD_ENOMEM, "host allocation");
+    std::unique_ptr<ld_ctx> guard(c);
+    c->kind = LD_MATFREE;
+    c->n = n;
+    c->dims[0] = (int32_t)std::min<int64_t>(n, INT32_MAX);
+    c->opt = opt;
+    c->nshift = n_shifts;
+    c->tol = tol;
+    c->user_bounds = true;
+    c->colour.assign(colouring, colouring + n);
+    c->ncolours = mx + 1;
+    c->ncols = c->ncolours;
+    c->T = 0;
+    c->engine = 3;
+    c->mf_terms.assign(c->ncolours, 0.0);
+    c->lmin = lambda_min;
+    c->lmax = lambda_max;
+    c->sigma.assign(n_shifts, 0.0);
+    c->alpha.assign(n_shifts, 0.0);
+    if (ld::hht_log_nodes(c->lmin, c->lmax, n_shifts, c->sigma.data(), c->alpha.data()) != 0)
+        return fail(LD_EINVAL, "bad spectral interval [%g, %g]", c->lmin, c->lmax);
+    c->cert = ld::hht_certificate(c->lmin, c->lmax, n_shifts, c->sigma.data(), c->alpha.data());
+    if (opt.cuda_stream) {
+        c->stream = static_cast<cudaStream_t>(opt.cuda_stream);
+    } else {
+        CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    const int e = ld::matfree_create(&c->mf, n, c->colour.data(), c->ncolours, n_shifts,
+                                     reinterpret_cast<void *>(matvec), user);
+    if (e != 0)
+        return fail(e == (int)cudaErrorMemoryAllocation ? LD_ENOMEM : LD_ECUDA, "matrix-free buffers: %s",
+                    cudaGetErrorString((cudaError_t)e));
+    *out = guard.release();
+    return LD_OK;
+}
+
 ld_status ld_set_params(ld_ctx *c, double kappa2, double tau, double scale) {
     if (!c) return fail(LD_EINVAL, "ctx is NULL");
     if (c->is_batch) return fail(LD_EINVAL, "batched context: use ld_batch_logdet");
+    REJECT_MATFREE(c);
     if (c->kind == LD_CSR) return fail(LD_EUNSUPPORTED, "CSR contexts have fixed values");
     if (!std::isfinite(kappa2) || kappa2 < 0.0) return fail(LD_EINVAL, "kappa2 must be finite and >= 0");
     if (!std::isfinite(tau) || tau < 0.0) return fail(LD_EINVAL, "tau must be finite and >= 0");
@@ -928,7 +1026,8 @@ ld_status ld_logdet(ld_ctx *c, double *logdet, ld_info *info) {
     if (!c || !logdet) return fail(LD_EINVAL, "ctx and logdet must be non-NULL");
     if (c->is_batch) return fail(LD_EINVAL, "batched context: use ld_batch_logdet");
     double out[2];
-    ld_status st = run_solve(c, 0, c->ncolours, c->opt.keep_x0 != 0, out, info);
+    ld_status st = c->mf ? run_matfree(c, 0, c->ncolours, out, info)
+                         : run_solve(c, 0, c->ncolours, c->opt.keep_x0 != 0, out, info);
     if (st == LD_OK) *logdet = out[0];
     return st;
 }
@@ -936,6 +1035,7 @@ ld_status ld_logdet(ld_ctx *c, double *logdet, ld_info *info) {
 ld_status ld_grad(ld_ctx *c, int n_params, const int *ids, double *grad) {
     if (!c || !grad) return fail(LD_EINVAL, "ctx and grad must be non-NULL");
     if (c->is_batch) return fail(LD_EINVAL, "batched context: use ld_batch_logdet");
+    REJECT_MATFREE(c);
     if (ld_status v = check_params(c, n_params, ids)) return v;
     if (!c->have_x0) return fail(LD_EINVAL, "no seed solutions saved: run ld_logdet on a keep_x0 context first");
     double *d_out = c->s.result + 2;
@@ -954,6 +1054,7 @@ ld_status ld_logdet_grad(ld_ctx *c, int n_params, const int *ids, double *logdet
                          ld_info *info) {
     if (!c || !logdet || !grad) return fail(LD_EINVAL, "ctx, logdet and grad must be non-NULL");
     if (c->is_batch) return fail(LD_EINVAL, "batched context: use ld_batch_logdet");
+    REJECT_MATFREE(c);
     if (ld_status v = check_params(c, n_params, ids)) return v;
     // d/d kappa2 of a scalar-kappa2 5/7-point grid is tr(Q^{-1}) * scale: the projected
     // seed sum v^T Q^{-1} v needs no stored seed vectors.
@@ -978,7 +1079,8 @@ ld_status ld_logdet_partial(ld_ctx *c, int cb, int ce, double *partial, ld_info 
     if (c->is_batch) return fail(LD_EINVAL, "batched context: use ld_batch_logdet");
     if (cb < 0 || ce < cb || ce > c->ncolours) return fail(LD_EINVAL, "colour range [%d, %d) outside [0, %d)", cb, ce, c->ncolours);
     double out[2];
-    ld_status st = run_solve(c, cb, ce, c->opt.keep_x0 != 0, out, info);
+    ld_status st = c->mf ? run_matfree(c, cb, ce, out, info)
+                         : run_solve(c, cb, ce, c->opt.keep_x0 != 0, out, info);
     if (st == LD_OK) *partial = out[0];
     return st;
 }
@@ -987,6 +1089,13 @@ ld_status ld_column_terms(const ld_ctx *c, double *terms, double *seed) {
     if (!c || !terms) return fail(LD_EINVAL, "ctx and terms must be non-NULL");
     if (c->is_batch) return fail(LD_EINVAL, "batched context: use ld_batch_logdet");
     if (!c->solved) return fail(LD_EINVAL, "no completed solve on this context");
+    if (c->mf) {   // the seed system is not followed: its projections are NaN
+        for (int k = 0; k < c->ncolours; ++k) {
+            terms[k] = c->mf_terms[k];
+            if (seed) seed[k] = NAN;
+        }
+        return LD_OK;
+    }
     CUDA_TRY(cudaMemcpy(terms, c->s.terms, c->ncolours * sizeof(double), cudaMemcpyDeviceToHost));
     if (seed) CUDA_TRY(cudaMemcpy(seed, c->s.pi0, c->ncolours * sizeof(double), cudaMemcpyDeviceToHost));
     return LD_OK;
@@ -1014,6 +1123,7 @@ ld_status ld_get_nodes(const ld_ctx *c, double *sigma, double *alpha, int32_t *n
 ld_status ld_apply(ld_ctx *c, int ncols, const double *x, double *y) {
     if (!c || !x || !y || ncols < 1) return fail(LD_EINVAL, "bad arguments");
     if (c->is_batch) return fail(LD_EINVAL, "batched context: use ld_batch_logdet");
+    REJECT_MATFREE(c);
     const int T = c->T;
     const int nt = (ncols + T - 1) / T;
     const int64_t n = c->n;
@@ -1056,6 +1166,7 @@ static ld_status funmv(ld_ctx *c, int ncols, const double *V, double *Y, ld_info
     Range range("ld vector form");
     if (!c || !V || !Y || ncols < 1) return fail(LD_EINVAL, "bad arguments");
     if (c->is_batch) return fail(LD_EINVAL, "batched context");
+    REJECT_MATFREE(c);
     const int T = c->T, N = c->nshift;
     const int nt = (ncols + T - 1) / T, C = nt * T;
     const int64_t n = c->n;
@@ -1169,6 +1280,7 @@ ld_status ld_logmv(ld_ctx *c, int ncols, const double *V, double *Y, ld_info *in
 ld_status ld_invsqrt_mv(ld_ctx *c, int ncols, const double *V, double *Y, ld_info *info) {
     if (!c) return fail(LD_EINVAL, "bad arguments");
     if (c->is_batch) return fail(LD_EINVAL, "batched context");
+    REJECT_MATFREE(c);
     std::vector<std::complex<double>> sg(c->nshift), be(c->nshift);
     if (ld::hht_invsqrt_nodes(c->lmin, c->lmax, c->nshift, sg.data(), be.data()) != 0)
         return fail(LD_EINVAL, "bad spectral interval [%g, %g]", c->lmin, c->lmax);

@@ -140,6 +140,25 @@ const char *engine_error_string(int cuda_err);
 void graph_distances(int kind, const int32_t dims[3], int periodic, int64_t n, const int64_t *rowptr,
                      const int32_t *colidx, int64_t j, int max_d, int32_t *dist);
 
+// ---------------------------------------------------------------- matrix-free operator
+// (matfree.cu) the caller supplies W = Q P; state and buffers of one context
+struct Matfree;
+struct MatfreeStats {
+    int iters;             // iterations run (maximum over columns)
+    int64_t column_iters;  // sum over columns of their iterations
+    int64_t launches;      // kernels launched (callback work not counted)
+    int callback_rc;       // nonzero return of the callback, if it stopped the solve
+    float ms;              // device time of the solve, callback included
+};
+// fn is an ld_matvec_fn; colour (host, n entries in [0, C)) is copied; 0 or a CUDA error
+int matfree_create(Matfree **out, int64_t n, const int32_t *colour, int C, int N, void *fn, void *user);
+void matfree_destroy(Matfree *m);
+// colours [cb, ce): terms_out[c - cb] = Re sum_l weight_l v_c^T (Q - sigma_l I)^{-1} v_c;
+// returns an ld_status (message through set_last_error)
+int matfree_solve(Matfree *m, int cb, int ce, const std::complex<double> *sigma,
+                  const std::complex<double> *weight, double tol, int max_iter, cudaStream_t stream,
+                  double *terms_out, MatfreeStats *st);
+
 // host: spectral interval of a CSR matrix (Gershgorin / half the converged smallest
 // Lanczos Ritz value; bounds.cpp); 0 on success, -1 when the estimate is not positive,
 // -2 when the Ritz value did not converge within the step cap; *steps = Lanczos steps run

@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(lib):
     assert len(syms) >= 20
     for s in syms:
         assert hasattr(lib, s), s
-    assert lib.ld_abi_version() == 3
+    assert lib.ld_abi_version() == 4
 
 
 @pytest.mark.parametrize("kind,dims,per,d", [
@@ -192,3 +192,32 @@ def test_csr_bounds_reject_indefinite(lib):
     with pytest.raises(L.LogDetError) as e:
         L.ld_csr_bounds(rp, ci, np.array([-1.0, -2.0]))
     assert e.value.status == L.LD_ENOTSPD
+
+
+def test_matfree_create_checks_arguments_before_any_device_call(lib):
+    """ld_create_matfree validates on the host (these run without a GPU)."""
+    n = 50
+    col = np.arange(n) % 3
+
+    def mv(P, W):
+        W.copy_(P)
+
+    bad = [
+        (dict(matvec=None), L.LD_EINVAL),
+        (dict(colouring=-col - 1), L.LD_EINVAL),
+        (dict(colouring=col + n), L.LD_EINVAL),
+        (dict(lambda_min=0.0), L.LD_EINVAL),
+        (dict(lambda_max=0.5), L.LD_EINVAL),
+        (dict(lambda_max=np.inf), L.LD_EINVAL),
+        (dict(n_shifts=0), L.LD_EINVAL),
+        (dict(tol=0.0), L.LD_EINVAL),
+        (dict(opts=L.options(precision=L.LD_MIXED)), L.LD_EUNSUPPORTED),
+        (dict(opts=L.options(max_iter=-1)), L.LD_EINVAL),
+    ]
+    for kw, status in bad:
+        args = dict(n=n, matvec=mv, colouring=col, lambda_min=1.0, lambda_max=2.0, n_shifts=8,
+                    tol=1e-8, opts=None)
+        args.update(kw)
+        with pytest.raises(L.LogDetError) as e:
+            L.ld_create_matfree(**args)
+        assert e.value.status == status, kw
