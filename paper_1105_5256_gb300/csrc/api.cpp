@@ -147,8 +147,10 @@ struct ld_ctx {
     // matrix-free operator (ld_create_matfree): the caller's W = Q P drives the solve
     ld::Matfree *mf = nullptr;
     std::vector<double> mf_terms;
+    bool l2_persist = false;   // captured kernels mark the colours persisting in L2
 
     ~ld_ctx() {
+        if (l2_persist) cudaCtxResetPersistingL2Cache();   // return those lines to normal
         if (mf) ld::matfree_destroy(mf);
         if (bgraph) cudaGraphExecDestroy(bgraph);
         for (ld_ctx *c : subs) delete c;
@@ -362,6 +364,55 @@ ld_status ensure_groups(ld_ctx *c) {
     return LD_OK;
 }
 
+// The colour array is read by every tile's pass.  With several tiles per pass its lines are
+// evicted by the streamed vectors between one tile's read and the next (on the 1024^2 Matern
+// the colours reached DRAM once per tile, 7 % of the pass traffic), so the captured kernels
+// mark it persisting in L2 (best effort: skipped where the device offers no persisting L2).
+void colour_persistence(ld_ctx *c, cudaGraph_t g) {
+    if (c->ntiles < 2 || !c->d_colour.p) return;
+    int dev = 0, maxp = 0, maxw = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, dev) != cudaSuccess ||
+        maxp <= 0 || maxw <= 0) {
+        cudaGetLastError();
+        return;
+    }
+    const size_t bytes = std::min(c->d_colour.bytes, (size_t)maxw);
+    size_t lim = 0;
+    if (cudaDeviceGetLimit(&lim, cudaLimitPersistingL2CacheSize) != cudaSuccess) lim = 0;
+    const size_t want = std::min(bytes, (size_t)maxp);
+    if (lim < want) {
+        if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want) != cudaSuccess ||
+            cudaDeviceGetLimit(&lim, cudaLimitPersistingL2CacheSize) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+    }
+    if (lim == 0) return;
+    cudaLaunchAttributeValue v{};
+    v.accessPolicyWindow.base_ptr = c->d_colour.p;
+    v.accessPolicyWindow.num_bytes = bytes;
+    v.accessPolicyWindow.hitRatio = (float)std::min(1.0, (double)lim / (double)bytes);
+    v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    size_t nn = 0;
+    if (cudaGraphGetNodes(g, nullptr, &nn) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn && cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess) {
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+                cudaGraphKernelNodeSetAttribute(nd, cudaLaunchAttributeAccessPolicyWindow, &v);
+        }
+    }
+    cudaGetLastError();
+    c->l2_persist = true;
+}
+
 ld_status ensure_graph(ld_ctx *c) {
     if (c->graph && c->graph_chunk == c->chunk) return LD_OK;
     invalidate_graph(c);
@@ -390,6 +441,7 @@ ld_status ensure_graph(ld_ctx *c) {
         return fail(LD_ECUDA, "capture: %s", ld::engine_error_string(err));
     }
     if (e2 != cudaSuccess) return fail(LD_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e2));
+    colour_persistence(c, g);
     cudaError_t e3 = cudaGraphInstantiate(&c->graph, g, 0);
     cudaGraphDestroy(g);
     if (e3 != cudaSuccess) {
