@@ -158,13 +158,13 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
 
 /* Matrix-free operator (Sec. 1: the method needs Q only through products Q v).
  * Enqueue W = Q P on `stream` (a cudaStream_t; or finish the product before returning).
- * P and W are device arrays of n x ncols doubles owned by the library, row-major (entry
+ * P_dev and W_dev are device arrays of n x ncols doubles owned by the library, row-major (entry
  * (i, c) at i * ncols + c; column c is the probing vector of colour colour_begin + c of
  * the solve); P is read-only, every entry of W must be written.  Called once per CG
  * iteration from the thread that called ld_logdet / ld_logdet_partial.  Return 0 on
  * success; anything else stops the solve with LD_ECALLBACK. */
-typedef int (*ld_matvec_fn)(void *user, int64_t n, int32_t ncols, const double *P, double *W,
-                            void *stream);
+typedef int (*ld_matvec_fn)(void *user, int64_t n, int32_t ncols, const double *P_dev,
+                            double *W_dev, void *stream);
 
 /* Create a context for an SPD operator given only by matvec (Sec. 2.1 method without a
  * matrix):
@@ -217,7 +217,9 @@ ld_status ld_logdet_partial(ld_ctx *ctx, int colour_begin, int colour_end, doubl
                             ld_info *info);
 
 /* Per-colour terms of the last solve: terms[c] = Re sum_l alpha_l v_c^T x^{sigma_l}_c
- * (n_colours doubles) and, if seed != NULL, seed[c] = v_c^T Q^{-1} v_c. */
+ * (n_colours doubles) and, if seed != NULL, seed[c] = v_c^T Q^{-1} v_c (NaN for a
+ * matrix-free context, whose seed system is not followed to convergence).
+ * LD_EINVAL before the first completed solve. */
 ld_status ld_column_terms(const ld_ctx *ctx, double *terms, double *seed);
 
 /* Colouring used by the context: colour (n int32), *n_colours. */
@@ -280,7 +282,8 @@ ld_status ld_colour_csr(int64_t n, const int64_t *rowptr, const int32_t *colidx,
                         int32_t *colour, int32_t *n_colours);
 
 /* Nodes of ld_invsqrt_mv's rational z^{-1/2} on [lmin, lmax]: the log nodes' poles sigma
- * and weights beta_j = -(2 i h / pi) w'(t_j), interleaved (re, im), N each. */
+ * and weights beta_j = -(2 i h / pi) w'(t_j), interleaved (re, im), N each (2N doubles per
+ * array).  LD_EINVAL unless 0 < lmin < lmax and 1 <= N <= 256. */
 ld_status ld_hht_invsqrt_nodes(double lmin, double lmax, int N, double *sigma, double *beta);
 
 /* Spectral interval a CSR context uses without user bounds: *lmax = Gershgorin bound of
