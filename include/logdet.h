@@ -286,6 +286,23 @@ ld_status ld_colour_csr(int64_t n, const int64_t *rowptr, const int32_t *colidx,
  * array).  LD_EINVAL unless 0 < lmin < lmax and 1 <= N <= 256. */
 ld_status ld_hht_invsqrt_nodes(double lmin, double lmax, int N, double *sigma, double *beta);
 
+/* P1 finite-element SPDE precision on a triangulation (general-mesh input for LD_CSR; the
+ * SPDE model of Sec. 3, tau (kappa - Laplacian) u = W with kappa^2 for kappa, on a mesh):
+ *   xy         n vertex coordinates (x, y), n x 2 row-major; 3 <= n < 2^31.
+ *   tri        m triangles as vertex indices, m x 3 row-major, either orientation.
+ *   alpha      1: Q = tau (kappa^2 C + G);  2: Q = tau K C^{-1} K with K = kappa^2 C + G,
+ *              C the lumped mass (a third of each incident triangle's area on the diagonal),
+ *              G the stiffness (integrals of grad phi_i . grad phi_j, Neumann boundary).
+ *   kappa2, tau > 0.
+ * Output: sorted CSR of Q (exact zeros dropped) in rowptr (n + 1), colidx and val (*nnz
+ * each), written only when capacity >= *nnz and all three are non-NULL; otherwise only
+ * *nnz is set (call once to size the arrays, then again to fill them).
+ * LD_EINVAL for bad sizes or parameters, an index outside [0, n), a zero-area triangle or
+ * a vertex in no triangle.  Host only. */
+ld_status ld_spde_fem_csr(int64_t n, const double *xy, int64_t m, const int64_t *tri, double kappa2,
+                          int alpha, double tau, int64_t capacity, int64_t *rowptr, int32_t *colidx,
+                          double *val, int64_t *nnz);
+
 /* Spectral interval a CSR context uses without user bounds: *lmax = Gershgorin bound of
  * scale * val, *lmin = half the smallest Ritz value of a Lanczos run from a fixed +-1 start
  * vector, run until that Ritz value has stagnated (less than 1e-3 relative change over the

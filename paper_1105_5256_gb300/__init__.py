@@ -110,6 +110,7 @@ def library(build_if_missing: bool = False):
         "ld_grid_bounds": ([P(Matrix), P(dbl), P(dbl)], st),
         "ld_csr_bounds": ([i64, vp, vp, vp, dbl, P(dbl), P(dbl)], st),
         "ld_hht_invsqrt_nodes": ([dbl, dbl, C.c_int, vp, vp], st),
+        "ld_spde_fem_csr": ([i64, vp, i64, vp, dbl, C.c_int, dbl, i64, vp, vp, vp, P(i64)], st),
         "ld_batch_create": ([C.c_int, vp, vp, C.c_int, dbl, P(Options), P(vp)], st),
         "ld_batch_logdet": ([vp, vp, vp, vp], st),
         "ld_logdet_static": ([P(Matrix), vp, C.c_int, C.c_int, dbl, C.c_int, vp, P(dbl)], st),

@@ -1462,6 +1462,32 @@ ld_status ld_hht_invsqrt_nodes(double lmin, double lmax, int N, double *sigma, d
     return LD_OK;
 }
 
+ld_status ld_spde_fem_csr(int64_t n, const double *xy, int64_t m, const int64_t *tri, double kappa2,
+                          int alpha, double tau, int64_t capacity, int64_t *rowptr, int32_t *colidx,
+                          double *val, int64_t *nnz) {
+    if (n < 3 || n > INT32_MAX || m < 1 || !xy || !tri || !nnz)
+        return fail(LD_EINVAL, "need 3 <= n < 2^31 vertices, m >= 1 triangles, xy, tri and nnz");
+    if (alpha != 1 && alpha != 2) return fail(LD_EINVAL, "alpha must be 1 or 2");
+    if (!(kappa2 > 0.0) || !std::isfinite(kappa2) || !(tau > 0.0) || !std::isfinite(tau))
+        return fail(LD_EINVAL, "kappa2 and tau must be positive and finite");
+    for (int64_t i = 0; i < 2 * n; ++i)
+        if (!std::isfinite(xy[i])) return fail(LD_EINVAL, "non-finite coordinate at %lld", (long long)(i / 2));
+    std::vector<int64_t> rp;
+    std::vector<int32_t> ci;
+    std::vector<double> vv;
+    const int rc = ld::fem_spde(n, xy, m, tri, kappa2, alpha, tau, rp, ci, vv);
+    if (rc == -1) return fail(LD_EINVAL, "triangle vertex index outside [0, n)");
+    if (rc == -2) return fail(LD_EINVAL, "degenerate triangle (zero area)");
+    if (rc == -3) return fail(LD_EINVAL, "a vertex belongs to no triangle");
+    *nnz = (int64_t)ci.size();
+    if (capacity >= *nnz && rowptr && colidx && val) {
+        std::copy(rp.begin(), rp.end(), rowptr);
+        std::copy(ci.begin(), ci.end(), colidx);
+        std::copy(vv.begin(), vv.end(), val);
+    }
+    return LD_OK;
+}
+
 ld_status ld_csr_bounds(int64_t n, const int64_t *rowptr, const int32_t *colidx, const double *val,
                         double scale, double *lmin, double *lmax) {
     if (n <= 0 || !rowptr || !colidx || !val || !lmin || !lmax) return fail(LD_EINVAL, "bad arguments");

@@ -4,6 +4,7 @@
 
 #include <complex>
 #include <cstdint>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -158,6 +159,12 @@ void matfree_destroy(Matfree *m);
 int matfree_solve(Matfree *m, int cb, int ce, const std::complex<double> *sigma,
                   const std::complex<double> *weight, double tol, int max_iter, cudaStream_t stream,
                   double *terms_out, MatfreeStats *st);
+
+// host: P1 finite-element SPDE precision of a triangulation as sorted CSR (fem.cpp);
+// 0, or -1 vertex index out of range, -2 degenerate triangle, -3 vertex in no triangle
+int fem_spde(int64_t n, const double *xy, int64_t m, const int64_t *tri, double kappa2, int alpha,
+             double tau, std::vector<int64_t> &rowptr, std::vector<int32_t> &colidx,
+             std::vector<double> &val);
 
 // host: spectral interval of a CSR matrix (Gershgorin / half the converged smallest
 // Lanczos Ritz value; bounds.cpp); 0 on success, -1 when the estimate is not positive,

@@ -9,8 +9,9 @@ vertex matrix) is pinned to facts of the finite-element spaces themselves:
     stiffness is the Neumann 5-point Laplacian, T (x) D + D (x) T, with T the 1D
     Neumann second difference and D = diag(1/2, 1, ..., 1, 1/2);
   * first-order matrix is SPD, the second-order one is K C~^{-1} K.
-The library's vectorised assembly (edge-vector formula) must equal the oracle's; the
-library's colouring and spectral interval run on the mesh graph.
+The library's native assembly (`ld_spde_fem_csr`, edge-vector formula) must equal the
+oracle's, pattern included; the library's colouring and spectral interval run on the mesh
+graph.
 """
 import numpy as np
 import pytest
@@ -105,7 +106,7 @@ def test_library_assembly_matches_oracle(seed, nx, ny, alpha):
     assert abs(sp.csr_matrix((vv2, ci2, rp2), shape=Qo.shape) - Qp).max() <= 1e-13 * abs(Qo).max()
 
 
-def test_library_assembly_rejects_bad_input():
+def test_library_assembly_rejects_bad_input(lib):
     p, t = synth.perturbed_triangulation(3, 5, 5)
     with pytest.raises(ValueError):
         mesh.spde_csr(p, t, 1.0, alpha=3)
@@ -113,12 +114,43 @@ def test_library_assembly_rejects_bad_input():
         mesh.spde_csr(p, t, 0.0)
     with pytest.raises(ValueError):
         mesh.spde_csr(p, t[:, :2], 1.0)
-    with pytest.raises(ValueError):
-        mesh.spde_csr(p, t + 100, 1.0)
     bad = t.copy()
     bad[0] = [0, 1, 2]                       # three collinear vertices on the lower edge
-    with pytest.raises(ValueError):
-        mesh.spde_csr(p, bad, 1.0)
+    orphan = np.concatenate([p, [[0.5, 0.5]]])   # a vertex in no triangle
+    for args in [(p, t + 100), (p, -t), (p, bad), (orphan, t)]:
+        with pytest.raises(L.LogDetError) as e:
+            mesh.spde_csr(*args, 1.0)
+        assert e.value.status == L.LD_EINVAL
+    # the C entry point checks its own arguments too (alpha, parameters, sizes)
+    nnz = np.zeros(1, dtype=np.int64)
+    P = np.ascontiguousarray(p)
+    T = np.ascontiguousarray(t, dtype=np.int64)
+    for a, k2, tau, n in [(3, 1.0, 1.0, len(p)), (1, -1.0, 1.0, len(p)), (1, 1.0, 0.0, len(p)),
+                          (2, 1.0, 1.0, 2)]:
+        st = lib.ld_spde_fem_csr(n, P.ctypes.data, len(T), T.ctypes.data, k2, a, tau, 0, None, None,
+                                 None, nnz.ctypes.data_as(L.C.POINTER(L.C.c_int64)))
+        assert st == L.LD_EINVAL
+
+
+@pytest.mark.parametrize("seed,nx,ny", MESHES)
+def test_library_assembly_query_then_fill(lib, seed, nx, ny):
+    """Two-call protocol: a capacity below nnz writes only nnz; the filled CSR has sorted
+    rows and the oracle's pattern exactly."""
+    p, t = synth.perturbed_triangulation(seed, nx, ny)
+    Q = om.fem_spde_precision(p, t, 2.0, 2)
+    P = np.ascontiguousarray(p)
+    T = np.ascontiguousarray(t, dtype=np.int64)
+    nnz = np.zeros(1, dtype=np.int64)
+    rp = np.full(len(p) + 1, -7, dtype=np.int64)
+    ci = np.zeros(Q.nnz - 1, dtype=np.int32)
+    vv = np.zeros(Q.nnz - 1)
+    nptr = nnz.ctypes.data_as(L.C.POINTER(L.C.c_int64))
+    assert lib.ld_spde_fem_csr(len(p), P.ctypes.data, len(T), T.ctypes.data, 2.0, 2, 1.0, Q.nnz - 1,
+                               rp.ctypes.data, ci.ctypes.data, vv.ctypes.data, nptr) == L.LD_OK
+    assert nnz[0] == Q.nnz and np.all(rp == -7)
+    rp2, ci2, vv2 = mesh.spde_csr(p, t, 2.0, 2)
+    assert np.array_equal(rp2, Q.indptr) and np.array_equal(ci2, Q.indices)
+    assert np.abs(vv2 - Q.data).max() <= 1e-13 * np.abs(Q.data).max()
 
 
 @pytest.mark.parametrize("alpha,d", [(1, 1), (1, 3), (2, 1), (2, 2)])
