@@ -1532,6 +1532,18 @@ ld_status ld_batch_create(int count, const ld_matrix *Qs, const int *distances, 
     ld_default_options(&opt);
     if (opt_in) opt = *opt_in;
     if (opt.precision != LD_FP64 && opt.precision != LD_MIXED) return fail(LD_EINVAL, "bad precision");
+    if (n_shifts < 1 || n_shifts > 256) return fail(LD_EINVAL, "n_shifts must be in [1, 256]");
+    if (!(tol > 0.0 && tol < 1.0)) return fail(LD_EINVAL, "tol must be in (0, 1)");
+    if (opt.max_iter < 0) return fail(LD_EINVAL, "max_iter must be >= 0");
+    // every instance is checked on the host before any device work
+    for (int i = 0; i < count; ++i) {
+        if (ld_status v = validate_matrix(&Qs[i])) {
+            std::string msg = g_err;
+            return fail(v, "instance %d: %s", i, msg.c_str());
+        }
+        if (Qs[i].kind == LD_CSR) return fail(LD_EUNSUPPORTED, "batched instances are grid kinds");
+        if (distances[i] < 0) return fail(LD_EINVAL, "instance %d: colouring_distance must be >= 0", i);
+    }
     ld_ctx *c = new (std::nothrow) ld_ctx();
     if (!c) return fail(LD_ENOMEM, "host allocation");
     std::unique_ptr<ld_ctx> guard(c);

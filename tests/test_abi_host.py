@@ -221,3 +221,25 @@ def test_matfree_create_checks_arguments_before_any_device_call(lib):
         with pytest.raises(L.LogDetError) as e:
             L.ld_create_matfree(**args)
         assert e.value.status == status, kw
+
+
+def test_batch_create_checks_every_instance_on_the_host(lib):
+    """ld_batch_create rejects bad shared arguments and bad instances before any device work."""
+    good = [L.grid_matrix(om.KIND_2D5, (16, 16), 0.5), L.grid_matrix(om.KIND_2D13_SQ, (12, 9), 0.2)]
+    rows, cols, w = synth.random_sparse_spd_pattern(1, 30)
+    csr = L.csr_matrix(*synth.csr_from_edges(30, rows, cols, w, 0.5))
+    cases = [
+        (dict(tol=0.0), L.LD_EINVAL),
+        (dict(n_shifts=0), L.LD_EINVAL),
+        (dict(opts=L.options(precision=5)), L.LD_EINVAL),
+        (dict(opts=L.options(max_iter=-2)), L.LD_EINVAL),
+        (dict(distances=[2, -1]), L.LD_EINVAL),
+        (dict(matrices=[good[0], csr]), L.LD_EUNSUPPORTED),
+        (dict(matrices=[good[0], L.grid_matrix(om.KIND_2D5, (0, 5), 0.5)]), L.LD_EINVAL),
+    ]
+    for kw, status in cases:
+        args = dict(matrices=good, distances=[2, 2], n_shifts=8, tol=1e-6, opts=None)
+        args.update(kw)
+        with pytest.raises(L.LogDetError) as e:
+            L.ld_batch_create(**args)
+        assert e.value.status == status, kw
