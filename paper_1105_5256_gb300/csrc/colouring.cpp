@@ -73,6 +73,14 @@ int colour_grid(int kind, const int32_t dims[3], int periodic, int d, int32_t *c
                 offs.push_back({dx, dy, dz});
             }
     const int64_t n = nx * ny * nz;
+    // Vertices whose ball needs no bounds or wrap logic take a fast path: their coloured
+    // neighbours are i + back[k], the same set the general path finds.  Without wrap the
+    // earlier half-ball must lie inside the grid; on a torus the whole ball must (a later
+    // offset that wraps lands on an earlier vertex).
+    std::vector<int64_t> back;
+    for (const Off &o : offs)
+        if (o.dz < 0 || (o.dz == 0 && (o.dy < 0 || (o.dy == 0 && o.dx < 0))))
+            back.push_back(o.dx + nx * (o.dy + ny * (int64_t)o.dz));
     std::vector<int64_t> used;
     int ncol = 0;
     for (int64_t i = 0; i < n; ++i) colour[i] = -1;
@@ -80,6 +88,21 @@ int colour_grid(int kind, const int32_t dims[3], int periodic, int d, int32_t *c
     for (int64_t z = 0; z < nz; ++z)
         for (int64_t y = 0; y < ny; ++y)
             for (int64_t x = 0; x < nx; ++x, ++i) {
+                bool inside = x >= R && x + R < nx && y >= R;
+                if (is3d) inside = inside && y + R < ny && z >= R;
+                if (periodic) inside = inside && y + R < ny && (!is3d || z + R < nz);
+                if (inside) {
+                    for (const int64_t dj : back) {
+                        const int32_t cj = colour[i + dj];
+                        if ((size_t)cj >= used.size()) used.resize((size_t)cj + 1, -1);
+                        used[cj] = i;
+                    }
+                    int32_t c = 0;
+                    while ((size_t)c < used.size() && used[c] == i) ++c;
+                    colour[i] = c;
+                    ncol = std::max(ncol, c + 1);
+                    continue;
+                }
                 for (const Off &o : offs) {
                     int64_t xx = x + o.dx, yy = y + o.dy, zz = z + o.dz;
                     if (periodic) {

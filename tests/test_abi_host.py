@@ -62,6 +62,23 @@ def test_grid_colouring_bit_exact(lib, kind, dims, per, d):
     assert nc == int(ref.max()) + 1
 
 
+def test_grid_colouring_random_shapes_bit_exact(lib):
+    """Seeded sweep over kinds, torus or Dirichlet, thin and tiny grids and distances 0-6:
+    the lattice colouring (fast interior path plus the bounds-checked edge path) equals the
+    oracle's breadth-first greedy colouring everywhere."""
+    rng = np.random.default_rng(7)
+    for trial in range(150):
+        kind = [om.KIND_2D5, om.KIND_2D13_SQ, om.KIND_3D7][trial % 3]
+        per = bool(rng.integers(0, 2))
+        nd = 3 if kind == om.KIND_3D7 else 2
+        dims = tuple(int(v) for v in rng.integers(1, 13 if nd == 3 else 40, size=nd))
+        d = int(rng.integers(0, 7))
+        ref = probing.colour_greedy(om.precision(kind, dims, 0.5, periodic=per), d)
+        col, nc = L.ld_colour_grid(kind, dims, per, d)
+        assert np.array_equal(col, ref), (kind, dims, per, d)
+        assert nc == int(ref.max()) + 1
+
+
 def test_csr_colouring_bit_exact(lib):
     n = 700
     rows, cols, w = synth.random_sparse_spd_pattern(11, n)
