@@ -10,12 +10,18 @@
   probed_rational_band sum_c Re sum_l alpha_l v_c^T (Q - sigma_l I)^{-1} v_c by
                        exact complex-symmetric banded LDL^T solves: the
                        method's target with no Krylov error.
+  probed_rational_splu the same target with each shifted system solved by a
+                       sparse LU factorisation (SuperLU, minimum-degree
+                       ordering): grids whose natural-order band is too wide
+                       for the banded solver (512^2 2D, 32^3 3D).
   spectral_bounds      the enclosing interval [m, M] used for the quadrature.
   logdet_method        the method in the paper's order: probing vectors from
                        the colouring (Sec. 2.1) -> rational nodes (Eq.
                        "eq_rat_app") -> CG-M per probing vector (Sec. 2.1) ->
                        sum of v_c^T f_N(Q) v_c; optional gradient terms
-                       (E v_c)^T Q^{-1} v_c from the seed solution.
+                       (E v_c)^T Q^{-1} v_c from the seed solution; optionally
+                       only a chosen subset of the colours (full-size grids,
+                       where every probing vector is an independent CG-M run).
 
 Reading of the spectral bounds (the paper only says extremal-eigenvalue
 estimates are needed): for Q = scale * (diag(kappa2) - Lap + tau diag(mask)),
@@ -31,6 +37,7 @@ from __future__ import annotations
 
 import numpy as np
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 from . import _native
 from .cgm import cgm
@@ -122,6 +129,32 @@ def probed_rational_band(Q: sp.csr_matrix, colour: np.ndarray, sigma, alpha,
     return terms if per_colour else float(terms.sum())
 
 
+def probed_rational_splu(Q: sp.csr_matrix, colour: np.ndarray, sigma, alpha,
+                         per_colour: bool = False):
+    """sum_c Re sum_l alpha_l v_c^T (Q - sigma_l I)^{-1} v_c with exact sparse solves.
+
+    Each shifted matrix Q - sigma_l I (complex symmetric) is factorised once by
+    SuperLU with a minimum-degree ordering of its symmetric pattern, and all
+    probing vectors are solved against it; v^T x is the bilinear form (no
+    conjugate), as in the Cauchy integral of Eq. "eq_rat_app".
+    """
+    n = Q.shape[0]
+    colour = np.asarray(colour)
+    C = int(colour.max()) + 1
+    V = np.zeros((n, C), dtype=np.complex128)
+    V[np.arange(n), colour] = 1.0
+    I = sp.identity(n, dtype=np.complex128, format="csc")
+    Qc = Q.astype(np.complex128).tocsc()
+    terms = np.zeros(C)
+    for s, al in zip(sigma, alpha):
+        lu = spla.splu((Qc - s * I).tocsc(), permc_spec="MMD_AT_PLUS_A",
+                       options={"SymmetricMode": True})
+        X = lu.solve(V)
+        q = np.sum(V * X, axis=0)
+        terms += np.real(al * q)
+    return terms if per_colour else float(terms.sum())
+
+
 def lap_extremes_1d(N: int, periodic: bool):
     if periodic:
         k = np.arange(N)
@@ -148,32 +181,38 @@ def spectral_bounds(kind: int, dims, kappa2, periodic: bool = False, tau: float 
 
 def logdet_method(Q: sp.csr_matrix, colour: np.ndarray, lmin: float, lmax: float,
                   n_shifts: int, tol: float, maxiter: int = 100000, grad_mats=(),
-                  per_colour: bool = False):
+                  per_colour: bool = False, colours=None):
     """Probing x rational approximation x CG-M, in the paper's order.
 
     Returns dict(logdet, grads, terms (per colour), iters (per colour)).
     grad_mats: list of E_eta = dQ/d eta; gradient estimate sum_c (E v_c)^T x0_c.
+    colours: run only these probing vectors (the others' terms stay NaN and the sums
+    cover the chosen ones); None runs all of them.
     """
     sigma, alpha = log_nodes(lmin, lmax, n_shifts)
     colour = np.asarray(colour)
     C = int(colour.max()) + 1
     n = Q.shape[0]
-    terms = np.zeros(C)
-    gterms = np.zeros((len(grad_mats), C))
+    run = range(C) if colours is None else [int(c) for c in colours]
+    terms = np.full(C, np.nan) if colours is not None else np.zeros(C)
+    gterms = np.full((len(grad_mats), C), np.nan) if colours is not None else np.zeros((len(grad_mats), C))
+    seeds = np.full(C, np.nan) if colours is not None else np.zeros(C)
     iters = np.zeros(C, dtype=np.int64)
     mv = Q.dot
-    for c in range(C):
+    for c in run:
         v = (colour == c).astype(np.float64)
         res = cgm(mv, v, -sigma, tol, maxiter)
         terms[c] = float(np.real(np.sum(alpha * res["pi"])))
+        seeds[c] = float(v @ res["x0"])
         iters[c] = res["iters"]
         for g, E in enumerate(grad_mats):
             gterms[g, c] = float((E @ v) @ res["x0"])
-    out = dict(logdet=float(terms.sum()), grads=gterms.sum(axis=1), iters=iters,
+    out = dict(logdet=float(np.nansum(terms)), grads=np.nansum(gterms, axis=1), iters=iters,
                sigma=sigma, alpha=alpha)
     if per_colour:
         out["terms"] = terms
         out["gterms"] = gterms
+        out["seeds"] = seeds
     return out
 
 

@@ -216,6 +216,91 @@ def test_banded_shifted_solves_equal_dense_rational_target():
     assert abs(band - dense) <= 1e-11 * abs(dense)
 
 
+@pytest.mark.parametrize("case", ["posterior2d", "field3d", "matern_periodic"])
+def test_sparse_lu_rational_target_equals_banded_and_dense(case):
+    """SuperLU shifted solves give the same rational target as the plain-C banded
+    LDL^T (an independent factorisation and ordering) and as dense eigh of f_N."""
+    import synth
+    if case == "posterior2d":
+        dims, kind, per = (30, 26), om.KIND_2D5, False
+        n = 780
+        mask = synth.obs_mask(4, n, 0.1)
+        Q = om.precision(kind, dims, 0.1, tau=4.0, mask=mask)
+        lo, hi = mt.spectral_bounds(kind, dims, 0.1, tau=4.0, mask=mask)
+        d = 4
+    elif case == "field3d":
+        dims, kind, per = (7, 6, 5), om.KIND_3D7, False
+        f = synth.kappa2_field(5, dims)
+        Q = om.precision(kind, dims, f)
+        lo, hi = mt.spectral_bounds(kind, dims, f)
+        d = 3
+    else:
+        dims, kind, per = (12, 10), om.KIND_2D13_SQ, True
+        Q = om.precision(kind, dims, 0.2, periodic=True)
+        lo, hi = mt.spectral_bounds(kind, dims, 0.2, periodic=True)
+        d = 2
+    col = probing.colour_greedy(Q, d)
+    sigma, alpha = hht.log_nodes(lo, hi, 20)
+    lu = mt.probed_rational_splu(Q, col, sigma, alpha, per_colour=True)
+    dense_total = mt.probed_dense(Q, col, lambda lam: hht.f_N(lam, sigma, alpha))
+    assert abs(lu.sum() - dense_total) <= 1e-11 * abs(dense_total)
+    if not per:   # wrap-around entries make the band as wide as the matrix
+        band = mt.probed_rational_band(Q, col, sigma, alpha, per_colour=True)
+        assert np.abs(lu - band).max() <= 1e-11 * np.abs(band).max()
+
+
+def test_method_on_a_subset_of_colours_equals_exact_solves():
+    """CG-M run for chosen probing vectors only: each chosen term equals the exact
+    rational target's term, the skipped ones are NaN and the seed projections are
+    v_c^T Q^{-1} v_c from a sparse LU solve."""
+    import synth
+    dims = (20, 18)
+    n = 360
+    f = synth.kappa2_field(9, dims)
+    Q = om.precision(om.KIND_2D5, dims, f)
+    col = probing.colour_greedy(Q, 3)
+    lo, hi = mt.spectral_bounds(om.KIND_2D5, dims, f)
+    pick = [0, 5, int(col.max())]
+    res = mt.logdet_method(Q, col, lo, hi, 20, 1e-13, per_colour=True, colours=pick)
+    exact = mt.probed_rational_band(Q, col, res["sigma"], res["alpha"], per_colour=True)
+    V = probing.probing_vectors(col)
+    X = sp.linalg.splu(Q.tocsc()).solve(V)
+    seeds = np.sum(V * X, axis=0)
+    for c in pick:
+        assert abs(res["terms"][c] - exact[c]) <= 1e-10 * abs(exact[c])
+        assert abs(res["seeds"][c] - seeds[c]) <= 1e-10 * abs(seeds[c])
+    skipped = [c for c in range(int(col.max()) + 1) if c not in pick]
+    assert np.all(np.isnan(res["terms"][skipped]))
+    assert abs(res["logdet"] - exact[pick].sum()) <= 1e-10 * np.abs(exact[pick]).sum()
+
+
+@pytest.mark.parametrize("what", ["field", "mask", "both"])
+@pytest.mark.parametrize("kind,dims,per", [(om.KIND_2D5, (9, 7), False), (om.KIND_2D5, (8, 6), True),
+                                          (om.KIND_3D7, (5, 4, 6), False),
+                                          (om.KIND_2D13_SQ, (7, 9), False)])
+def test_spectral_bounds_enclose_field_and_mask_spectrum(kind, dims, per, what):
+    """With a kappa^2 field and/or an observation mask the interval [m, M] must still
+    enclose the spectrum (dense eigvalsh), and each end must lie within the field's
+    spread (plus tau) of it.  A bound built from the wrong end of the field, or one
+    that drops the mask's tau, fails one of the two."""
+    import synth
+    if kind == om.KIND_2D13_SQ and what != "field":
+        pytest.skip("the Matern kind has no observation term")
+    n = int(np.prod(dims))
+    f = 0.6 * synth.kappa2_field(11, dims, sd=2.0) if what != "mask" else np.full(n, 0.3)
+    mask = synth.obs_mask(12, n, 0.5) if what != "field" else None
+    tau = 10.0 if mask is not None else 0.0
+    Q = om.precision(kind, dims, f, periodic=per, tau=tau, mask=mask)
+    ev = np.linalg.eigvalsh(Q.toarray())
+    lo, hi = mt.spectral_bounds(kind, dims, f, periodic=per, tau=tau, mask=mask)
+    assert lo <= ev.min() * (1 + 1e-12) and ev.max() <= hi * (1 + 1e-12)
+    spread = f.max() - f.min() + tau
+    if kind == om.KIND_2D13_SQ:   # bounds of the square: compare square roots
+        assert np.sqrt(lo) >= np.sqrt(ev.min()) - spread and np.sqrt(hi) <= np.sqrt(ev.max()) + spread
+    else:
+        assert lo >= ev.min() - spread and hi <= ev.max() + spread
+
+
 # ---------------------------------------------------------------- distance selection
 @pytest.mark.parametrize("kind,dims,per", [(om.KIND_2D5, (12, 10), False), (om.KIND_2D5, (9, 8), True),
                                           (om.KIND_2D13_SQ, (11, 9), False)])
