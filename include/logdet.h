@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define LD_ABI_VERSION 4
+#define LD_ABI_VERSION 5
 
 typedef struct ld_ctx ld_ctx;
 
@@ -111,6 +111,13 @@ typedef struct {
                                  x_lo, x_lo = 0 and every active tile's residual is replaced
                                  by v - Q x_hi formed with FP64 arithmetic.  Keeps x0 on the
                                  device (as keep_x0).  0 = off. */
+    int32_t lattice_pass;     /* grid engine, FP32 vectors on a 2D lattice, tiles of 2 or 4
+                                 columns: 0 = the lean pass (the solve state is r and p, or r
+                                 and Q1 p for the Matern kind; Q p is recomputed each pass: 4
+                                 words per vertex and column per pass) wherever it applies
+                                 (not for the Matern kind while x0 is kept); 1 = always the
+                                 stored-w pass (r, Q p, p: 6 words).  Results agree to
+                                 rounding. */
 } ld_options;
 
 typedef struct {
@@ -133,6 +140,12 @@ typedef struct {
     double rel_resid_max;     /* when x0 is kept (keep_x0, a gradient or reliable_delta > 0):
                                  max over the call's columns of ||v_c - Q x_c|| / ||v_c||, the
                                  true seed residual formed in FP64; -1 otherwise */
+    int32_t pass_words;       /* grid engine: vector words per vertex and probing vector that
+                                 one CG pass reads plus writes for the solve state -- 4 for the
+                                 lean lattice pass (FP32 on 2D lattices: r and p, or r and Q1 p
+                                 for the Matern kind, with Q p recomputed), 6 for the stored-w
+                                 pass (r, Q p, p), plus 2 when the pass also updates the kept
+                                 seed solution; -1 for the other engines */
 } ld_info;
 
 /* ABI version (LD_ABI_VERSION).  Never fails. */

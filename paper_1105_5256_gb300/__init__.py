@@ -50,7 +50,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("tile_width", C.c_int32), ("max_iter", C.c_int32),
                 ("keep_x0", C.c_int32), ("lambda_min", C.c_double), ("lambda_max", C.c_double),
                 ("cuda_stream", C.c_void_p), ("colouring", C.c_void_p), ("engine", C.c_int32),
-                ("chunk_iters", C.c_int32), ("reliable_delta", C.c_double)]
+                ("chunk_iters", C.c_int32), ("reliable_delta", C.c_double),
+                ("lattice_pass", C.c_int32)]
 
 
 class Info(C.Structure):
@@ -59,7 +60,8 @@ class Info(C.Structure):
                 ("lambda_min", C.c_double), ("lambda_max", C.c_double), ("quad_cert", C.c_double),
                 ("ms", C.c_double), ("iter_ms", C.c_double), ("tile_iters", C.c_int64),
                 ("gpu_launches", C.c_int64), ("bulk_rows", C.c_int32),
-                ("reliable_updates", C.c_int32), ("rel_resid_max", C.c_double)]
+                ("reliable_updates", C.c_int32), ("rel_resid_max", C.c_double),
+                ("pass_words", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

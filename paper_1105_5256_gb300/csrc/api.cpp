@@ -113,6 +113,9 @@ struct ld_ctx {
     DevBuf d_r[2], d_w[2], d_p[2], d_x;
     DevBuf d_xhi, d_norm2;   // reliable updates: FP64 seed solution part; residual norms
     DevBuf d_diag_d, d_diag_f;   // per-vertex diagonal term (field and/or mask models)
+    DevBuf d_lane;     // lane codes of the lean lattice pass (built on first use)
+    bool lane_built = false;   // d_lane holds the lane codes of this context's colouring
+    int lean_plan_x0 = -1;     // keep_x0 the current lean plan was made for
     DevBuf d_colscal;  // 8 double arrays [ncols]
     DevBuf d_colint;   // 2 int arrays [ncols]
     DevBuf d_shift;    // 4 double2 arrays [ncols*N] + uint8 [ncols*N]
@@ -472,6 +475,9 @@ void fill_info(const ld_ctx *c, ld_info *info, ld_status st, int iters, float ms
     info->bulk_rows = c->engine == 1 && lattice2d && !c->mf ? c->s.bulk : -1;
     info->reliable_updates = 0;
     info->rel_resid_max = -1.0;
+    info->pass_words = -1;
+    if (c->engine == 1 && !c->mf && !c->is_batch)
+        info->pass_words = (lattice2d && c->s.lean ? 4 : 6) + (c->s.keep_x0 ? 2 : 0);
 }
 
 // matrix-free contexts support ld_logdet, ld_logdet_partial and the getters only
@@ -540,6 +546,21 @@ ld_status run_solve(ld_ctx *c, int cb, int ce, bool keep_x0, double out[2], ld_i
     const int want_x0 = keep_x0 ? 1 : 0;
     if (c->s.keep_x0 != want_x0) {
         c->s.keep_x0 = want_x0;
+        invalidate_graph(c);
+    }
+    // the lean lattice pass (four state words per vertex and column) wherever it applies;
+    // the stored-w pass otherwise (FP64, other kinds, the Matern kind with a kept x0)
+    const int want_lean = c->engine == 1 && c->opt.lattice_pass == 0 ? ld::engine_lean_x(c->s, keep_x0) : 0;
+    if (c->s.lean != want_lean || (want_lean && c->lean_plan_x0 != want_x0)) {
+        c->s.lean = want_lean;
+        ld::engine_plan(c->s);           // the lean plan's occupancy depends on keep_x0
+        c->lean_plan_x0 = want_x0;
+        if (want_lean && !c->lane_built) {
+            CUDA_TRY(c->d_lane.alloc(ld::engine_lean_code_bytes(c->s)));
+            ENGINE_TRY(ld::engine_lean_codes(c->s, c->d_lane.as<uint8_t>(), c->stream));
+            c->lane_built = true;
+        }
+        c->s.lane = want_lean ? c->d_lane.as<uint8_t>() : nullptr;
         invalidate_graph(c);
     }
     c->have_x0 = false;
@@ -660,9 +681,9 @@ std::mutex g_tune_mu;
 std::map<std::string, int> g_tune;
 bool g_tune_loaded = false;
 
-std::string tune_key(const ld_matrix *Q, int precision, int ncolours) {
+std::string tune_key(const ld_matrix *Q, int precision, int lattice_pass, int ncolours) {
     std::ostringstream k;
-    k << Q->kind << ":" << precision << ":" << (Q->periodic ? 1 : 0) << ":" << Q->dims[0] << "x"
+    k << Q->kind << ":" << precision << (lattice_pass ? "w" : "") << ":" << (Q->periodic ? 1 : 0) << ":" << Q->dims[0] << "x"
       << Q->dims[1] << "x" << (Q->kind == LD_STENCIL_3D7 ? Q->dims[2] : 1) << ":" << ncolours
       << (Q->kappa2_field ? ":field" : "") << (Q->obs_mask ? ":mask" : "");
     return k.str();
@@ -707,7 +728,7 @@ void tune_save_locked() {
 
 int autotune_tile(const ld_matrix *Q, int d, int N, double tol, const ld_options &opt,
                   const std::vector<int32_t> &colour, int ncolours) {
-    const std::string key = tune_key(Q, opt.precision, ncolours);
+    const std::string key = tune_key(Q, opt.precision, opt.lattice_pass, ncolours);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         tune_load_locked();
@@ -795,6 +816,7 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
     if (opt.chunk_iters < 0 || opt.chunk_iters > 4096) return fail(LD_EINVAL, "chunk_iters out of range");
     if (!(opt.reliable_delta >= 0.0 && opt.reliable_delta < 1.0))
         return fail(LD_EINVAL, "reliable_delta must be in [0, 1)");
+    if (opt.lattice_pass < 0 || opt.lattice_pass > 1) return fail(LD_EINVAL, "lattice_pass must be 0 or 1");
 
     ld_ctx *c = new (std::nothrow) ld_ctx();
     if (!c) return fail(LD_ENOMEM, "host allocation");
@@ -974,8 +996,17 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
     s.terms = c->d_terms.as<double>();
     s.class_size = s.terms + C;
     s.result = s.terms + 2 * C;
-    ld::engine_plan(s);
-    const size_t part = std::max<size_t>((size_t)c->ntiles * s.bpt * ld::NDOT * c->T, (size_t)152 * 4 * 3);
+    s.lean = 0;
+    s.lane = nullptr;
+    int bpt_max = 0;
+    for (int kx = 0; kx < 2; ++kx) {   // the lean lattice pass plans its own strips
+        Solve t = s;
+        t.keep_x0 = kx;
+        t.lean = ld::engine_lean_x(s, kx != 0);
+        if (t.lean && c->engine == 1 && opt.lattice_pass == 0) bpt_max = std::max(bpt_max, ld::engine_plan(t));
+    }
+    bpt_max = std::max(bpt_max, ld::engine_plan(s));
+    const size_t part = std::max<size_t>((size_t)c->ntiles * bpt_max * ld::NDOT * c->T, (size_t)152 * 4 * 3);
     CUDA_TRY(c->d_partial.alloc(part * sizeof(double)));
     s.partial = c->d_partial.as<double>();
     CUDA_TRY(cudaMemset(c->d_tile.p, 0, c->d_tile.bytes));

@@ -2,6 +2,7 @@
 // vector initialisation, the one-CTA and batched persistent engines, the
 // vector form (log(Q) V), operator application, gradients (sm_103a).
 #include "engine_device.cuh"
+#include "engine_lean.cuh"
 
 namespace ld {
 
@@ -699,17 +700,84 @@ struct ApplyLauncher {
     }
 };
 
+int engine_lean_x(const Solve &s, bool keep_x0) {
+    const int k = s.op.kind;
+    if (s.precision != 1 || (k != KIND_2D5 && k != KIND_2D13_SQ) || (s.T != 2 && s.T != 4)) return 0;
+    if (s.asig) return 0;                               // shifted-vector mode reads w
+    if (k == KIND_2D13_SQ && keep_x0) return 0;         // the Matern state holds no p
+    // two columns a thread at T = 2 on even widths (16-byte aligned pairs), else one
+    return s.T == 2 && s.op.nx % 2 == 0 ? 2 : 1;
+}
+
+namespace {
+void lean_geom(const Solve &s, int &swl, int &xh, int &w) {
+    const int X = s.lean;
+    if (s.op.kind == KIND_2D13_SQ) {
+        swl = LEAN_NT * X;
+        xh = LeanGeom<KIND_2D13_SQ>::XH;
+    } else {
+        swl = LEAN_NT * X;
+        xh = LeanGeom<KIND_2D5>::XH;
+    }
+    w = swl - 2 * xh;
+}
+}  // namespace
+
+size_t engine_lean_code_bytes(const Solve &s) {
+    if (s.lean <= 0) return 0;
+    int swl, xh, w;
+    lean_geom(s, swl, xh, w);
+    return (size_t)s.ntiles * s.strips * s.op.ny * swl;
+}
+
+// Lane codes of the lean pass in strip layout, [tile][strip][row][SWL]: colour - tile*T
+// when that is a column of the tile and the vertex is owned by the strip, else LEAN_NONE
+// (halo and out-of-grid columns)
+__global__ void k_lean_codes(const int32_t *colour, int nx, int ny, int T, int ntiles, int strips,
+                             int SWL, int XH, int W, uint8_t *out) {
+    const int64_t total = (int64_t)ntiles * strips * ny * SWL;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int xl = (int)(q % SWL);
+        int64_t r = q / SWL;
+        const int y = (int)(r % ny);
+        r /= ny;
+        const int strip = (int)(r % strips);
+        const int tile = (int)(r / strips);
+        const int gx = strip * W - XH + xl;
+        uint8_t c = LEAN_NONE;
+        if (xl >= XH && xl < XH + W && gx < nx) {
+            const int lc = colour[(int64_t)y * nx + gx] - tile * T;
+            if (lc >= 0 && lc < T) c = (uint8_t)lc;
+        }
+        out[q] = c;
+    }
+}
+
+int engine_lean_codes(const Solve &s, uint8_t *out, void *stream) {
+    int swl, xh, w;
+    lean_geom(s, swl, xh, w);
+    const int64_t total = (int64_t)s.ntiles * s.strips * s.op.ny * swl;
+    int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    if (blocks < 1) blocks = 1;
+    k_lean_codes<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        s.colour, s.op.nx, s.op.ny, s.T, s.ntiles, s.strips, swl, xh, w, out);
+    return (int)cudaGetLastError();
+}
+
 int engine_plan(Solve &s) {
     int dev = 0, sms = 152, occ = 8;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const bool lattice2d = s.op.kind == KIND_2D5 || s.op.kind == KIND_2D13_SQ;
+    if (!lattice2d || s.precision != 1 || s.asig) s.lean = 0;   // shifted-vector mode reads w
     // bulk row copies measured faster for packs of 24 bytes and more; per-thread
     // copies win for 8- and 16-byte packs (fewer instructions on the critical path)
     const int pack_bytes = s.T * (s.precision == 0 ? (int)sizeof(double) : (int)sizeof(float));
-    s.bulk = lattice2d && pack_bytes >= 24 && stream_bulk_ok(s.op.nx, pack_bytes);
-    const int oe = s.precision == 0 ? iteration_occupancy<double>(s.T, s.op.kind, s.bulk != 0, &occ)
-                                    : iteration_occupancy<float>(s.T, s.op.kind, s.bulk != 0, &occ);
+    s.bulk = lattice2d && !s.lean && pack_bytes >= 24 && stream_bulk_ok(s.op.nx, pack_bytes);
+    const int oe = s.precision == 0
+                       ? iteration_occupancy<double>(s.T, s.op.kind, s.bulk != 0, 0, s.keep_x0 != 0, &occ)
+                       : iteration_occupancy<float>(s.T, s.op.kind, s.bulk != 0, s.lean, s.keep_x0 != 0, &occ);
     if (oe != 0 || occ < 1) occ = 1;
     // one resident wave; with several tiles (tile groups run concurrently on their own
     // streams) 1.5 waves, so that CTAs of one group fill the gaps of another
@@ -717,8 +785,12 @@ int engine_plan(Solve &s) {
     if (s.ntiles >= 2) target = target * 3 / 2;
     s.strips = 1;
     s.seg = 1;
-    if (s.op.kind == KIND_2D5 || s.op.kind == KIND_2D13_SQ) {
-        const int W = s.op.kind == KIND_2D13_SQ ? Strip<KIND_2D13_SQ>::W : Strip<KIND_2D5>::W;
+    if (lattice2d) {
+        int W = s.op.kind == KIND_2D13_SQ ? Strip<KIND_2D13_SQ>::W : Strip<KIND_2D5>::W;
+        if (s.lean) {
+            int swl, xh;
+            lean_geom(s, swl, xh, W);
+        }
         s.strips = (s.op.nx + W - 1) / W;
         int64_t nsegs = target / ((int64_t)s.strips * s.ntiles);
         if (nsegs < 1) nsegs = 1;

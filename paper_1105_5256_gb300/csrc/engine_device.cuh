@@ -1538,6 +1538,6 @@ static int dispatch(int precision, int T, int kind, A &&...args) {
 template <typename V>
 int iteration_launch(const Solve &s, int cur, cudaStream_t st);
 template <typename V>
-int iteration_occupancy(int T, int kind, bool bulk, int *occ);
+int iteration_occupancy(int T, int kind, bool bulk, int lean, bool keepx, int *occ);
 
 }  // namespace ld

@@ -2,8 +2,49 @@
 // precision by engine_iter_f32.cu and engine_iter_f64.cu.
 #pragma once
 #include "engine_device.cuh"
+#include "engine_lean.cuh"
 
 namespace ld {
+
+// the lean pass exists for FP32 vectors, tiles of 2 or 4 columns, on 2D lattices
+template <typename V, int T, int KIND>
+constexpr bool has_lean() {
+    return std::is_same<V, float>::value && (T == 2 || T == 4) &&
+           (KIND == KIND_2D5 || KIND == KIND_2D13_SQ);
+}
+
+template <int T, int X, int KIND>
+int lean_launch(const Solve &s, dim3 grid, int cur, cudaStream_t st) {
+    if constexpr (KIND == KIND_2D5) {
+        if (s.keep_x0) {
+            k_lean2d<T, X, KIND, true><<<grid, LEAN_NT, LeanSmem<T, X, KIND, true>::bytes, st>>>(s, cur);
+            return (int)cudaGetLastError();
+        }
+    }
+    k_lean2d<T, X, KIND, false><<<grid, LEAN_NT, LeanSmem<T, X, KIND, false>::bytes, st>>>(s, cur);
+    return (int)cudaGetLastError();
+}
+
+// resident CTAs per SM of the lean pass (sets the shared-memory opt-in of its variants)
+template <int T, int X, int KIND>
+int lean_occupancy(int *out, bool keepx) {
+    constexpr size_t sm0 = LeanSmem<T, X, KIND, false>::bytes;
+    if (cudaFuncSetAttribute(k_lean2d<T, X, KIND, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm0) != cudaSuccess)
+        return (int)cudaGetLastError();
+    if constexpr (KIND == KIND_2D5) {
+        constexpr size_t sm1 = LeanSmem<T, X, KIND, true>::bytes;
+        if (cudaFuncSetAttribute(k_lean2d<T, X, KIND, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm1) != cudaSuccess)
+            return (int)cudaGetLastError();
+        if (keepx) {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_lean2d<T, X, KIND, true>, LEAN_NT, sm1);
+            return (int)cudaGetLastError();
+        }
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_lean2d<T, X, KIND, false>, LEAN_NT, sm0);
+    return (int)cudaGetLastError();
+}
 
 template <typename V, int T, int KIND>
 struct IterLauncher {
@@ -12,6 +53,12 @@ struct IterLauncher {
         const int nt = s.tile0 < s.ntiles ? (s.ntiles - s.tile0 + ts - 1) / ts : 0;
         if (nt == 0) return 0;
         dim3 grid(s.bpt, nt);
+        if constexpr (has_lean<V, T, KIND>()) {
+            if (s.lean == 1) return lean_launch<T, 1, KIND>(s, grid, cur, st);
+            if constexpr (T == 2) {
+                if (s.lean == 2) return lean_launch<T, 2, KIND>(s, grid, cur, st);
+            }
+        }
         if constexpr (KIND == KIND_2D5 || KIND == KIND_2D13_SQ) {
             constexpr int G = stream_groups<V, T>();
             constexpr size_t sm = stream_smem_bytes<V, T, G, KIND>(), smb = stream_bulk_smem_bytes<V, T>();
@@ -40,8 +87,14 @@ struct IterLauncher {
 template <typename V, int T, int KIND>
 struct OccLauncher {
     // resident CTAs per SM of the iteration kernels (the smaller of the two phases)
-    static int run(int *out, bool bulk) {
+    static int run(int *out, bool bulk, int lean, bool keepx) {
         int a = 0, b = 0;
+        if constexpr (has_lean<V, T, KIND>()) {
+            if (lean == 1) return lean_occupancy<T, 1, KIND>(out, keepx);
+            if constexpr (T == 2) {
+                if (lean == 2) return lean_occupancy<T, 2, KIND>(out, keepx);
+            }
+        }
         if constexpr (KIND == KIND_2D5 || KIND == KIND_2D13_SQ) {
             constexpr int G = stream_groups<V, T>();
             constexpr size_t sm = stream_smem_bytes<V, T, G, KIND>(), smb = stream_bulk_smem_bytes<V, T>();
@@ -81,8 +134,8 @@ int iteration_launch(const Solve &s, int cur, cudaStream_t st) {
 }
 
 template <typename V>
-int iteration_occupancy(int T, int kind, bool bulk, int *occ) {
-    return dispatch_v<V, OccLauncher>(T, kind, occ, bulk);
+int iteration_occupancy(int T, int kind, bool bulk, int lean, bool keepx, int *occ) {
+    return dispatch_v<V, OccLauncher>(T, kind, occ, bulk, lean, keepx);
 }
 
 }  // namespace ld

@@ -3,5 +3,5 @@
 
 namespace ld {
 template int iteration_launch<float>(const Solve &, int, cudaStream_t);
-template int iteration_occupancy<float>(int, int, bool, int *);
+template int iteration_occupancy<float>(int, int, bool, int, bool, int *);
 }  // namespace ld

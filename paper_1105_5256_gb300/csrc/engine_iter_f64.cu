@@ -3,5 +3,5 @@
 
 namespace ld {
 template int iteration_launch<double>(const Solve &, int, cudaStream_t);
-template int iteration_occupancy<double>(int, int, bool, int *);
+template int iteration_occupancy<double>(int, int, bool, int, bool, int *);
 }  // namespace ld

@@ -73,6 +73,10 @@ struct Solve {
     int bpt;               // CTAs per tile (grid engine)
     int strips, seg;       // 2D kinds: lattice strips per tile, rows per CTA segment
     int bulk;              // 2D kinds: rows arrive by bulk (TMA) copies (alignment permits)
+    int lean;              // 2D kinds, FP32: 0 the stored-w pass (state r, w, p); X > 0 the
+                           // lean pass (state r and p, or r and u = Q1 p for the Matern
+                           // kind; w recomputed), X lattice columns per thread
+    const uint8_t *lane;   // lean pass: per-tile lane codes in strip layout (or null)
     int tile0, tstride;    // grid engine: a launch covers tiles tile0, tile0 + tstride, ...
                            // (grid.y of them; tstride 0 reads as 1)
     int precision;         // 0 fp64, 1 mixed
@@ -134,7 +138,13 @@ int engine_fill_diag(const Operator &op, double *diag_d, float *diag_f, void *st
 // ||v_c - Q x_c||^2 in FP64 for c in [col_begin, col_end), x = x_hi when present, else x.
 int engine_true_residual(const Solve &s, int set, int col_begin, int col_end, int replace,
                          double *norm2_dev, void *stream);
-int engine_plan(Solve &s);   // sets bpt (and strips/seg); returns bpt
+int engine_plan(Solve &s);   // sets bpt (and strips/seg) for s.lean's pass; returns bpt
+// lean pass: lattice columns per thread it uses for this solve's kind, precision, tile
+// width and grid (0: not available; the stored-w pass runs)
+int engine_lean_x(const Solve &s, bool keep_x0);
+// bytes of the lane codes for the current plan (s.lean > 0), and their construction
+size_t engine_lean_code_bytes(const Solve &s);
+int engine_lean_codes(const Solve &s, uint8_t *out, void *stream);
 const char *engine_error_string(int cuda_err);
 
 // host: graph distances from vertex j (colouring.cpp)

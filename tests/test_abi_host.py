@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(lib):
     assert len(syms) >= 20
     for s in syms:
         assert hasattr(lib, s), s
-    assert lib.ld_abi_version() == 4
+    assert lib.ld_abi_version() == 5
 
 
 @pytest.mark.parametrize("kind,dims,per,d", [
