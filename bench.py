@@ -125,46 +125,177 @@ def colour_ranges(n_colours: int, world: int):
     return out
 
 
-def algorithmic_bytes(n, T, prec, tile_iters, passes):
+def algorithmic_bytes(n, T, word, tile_iters, keep_x=False, bq_per_pass=0, passes=0):
     """Algorithmic HBM bytes of the CG passes of a solve.
 
-    A pass reads r, w, p of one set and writes r, w, p of the other: 6 vector passes of
-    n*T words per active tile (tile_iters counts tile-passes), plus each vertex's colour
-    once per pass (4 bytes).  Halo re-reads are not counted.
+    A pass reads the CG state of every vertex and probing vector once and writes it
+    once: r and p (4 words), plus x in gradient mode (2 words); the matrix adds its own
+    bytes once per pass (0 for a constant-coefficient stencil, one word a vertex for a
+    kappa^2 field, one byte a vertex for an observation mask).  tile_iters counts
+    tile-passes of T columns each.
     """
-    w = 8 if prec == "fp64" else 4
-    return 6 * n * T * w * tile_iters + 4 * n * passes
+    return (4 + (2 if keep_x else 0)) * n * T * word * tile_iters + bq_per_pass * passes
+
+
+def moved_bytes(n, T, word, tile_iters, pass_words, lean):
+    """Bytes the pass kernel moves (halo re-reads aside): its state words per vertex and
+    column (ld_info.pass_words: 4 for the lean pass, 6 for the stored-w pass, 2 more with
+    x) and per vertex the tile's lane code (1 byte, lean pass) or colour (4 bytes)."""
+    return (pass_words * T * word + (1 if lean else 4)) * n * tile_iters
 
 
 def pass_kernel_sha256():
     """sha256 over the sources of the pass kernels (device code and their launcher)."""
     import hashlib
     h = hashlib.sha256()
-    for name in ("engine_device.cuh", "engine_iter.cuh"):
+    for name in ("engine_device.cuh", "engine_lean.cuh", "engine_iter.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1105_5256_gb300", "csrc", name), "rb").read())
     return h.hexdigest()
 
 
-def recorded_traffic(tile_width):
-    """DRAM bytes per full launch of the pass kernel from the committed ncu summary, or
-    None when the engine source changed since that capture (or no summary matches)."""
-    import hashlib
-    path = os.path.join(ROOT, "profiles", "k_stream2d_matern1024_T%d.md" % tile_width)
+def recorded_traffic(profile):
+    """DRAM bytes (read + write) of one CG pass from a committed ncu summary under
+    profiles/, or None when the pass kernels' sources changed since that capture (or the
+    summary is missing)."""
+    path = os.path.join(ROOT, "profiles", profile)
     try:
         rec = dict(line.split(": ", 1) for line in open(path).read().splitlines()
-                   if line.startswith(("engine_sha256: ", "traffic_bytes_per_launch: ")))
-        cur = pass_kernel_sha256()
-        if rec.get("engine_sha256", "").strip() != cur:
+                   if line.startswith(("engine_sha256: ", "traffic_bytes_per_pass: ")))
+        if rec.get("engine_sha256", "").strip() != pass_kernel_sha256():
             return None
-        return float(rec["traffic_bytes_per_launch"])
+        return float(rec["traffic_bytes_per_pass"])
     except (OSError, KeyError, ValueError):
         return None
 
 
+def combine_partials(vec):
+    """Sum one evaluation's per-rank partial results (log det, then gradient components)
+    over the ranks: the one exchange of the colour split (Sec. 2.1, one probing vector per
+    node), a single all-reduce of 1 + n_params doubles."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(vec, dtype=torch.float64)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        if dist.get_backend() == "nccl":
+            t = t.cuda()
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t.cpu()]
+
+
+def timed_evals(L, ctx, count, params=None, grad=None):
+    """Evaluate `count` times (optionally setting kappa^2 etc. first); returns the device
+    time (ms), the time inside the CG passes (ms), tile-passes, passes and the last info."""
+    ms = it_ms = 0.0
+    tile_iters = passes = 0
+    info = v = g = None
+    for k in range(count):
+        if params is not None:
+            L.ld_set_params(ctx, *params[k % len(params)])
+        if grad:
+            v, g, info = L.ld_logdet_grad(ctx, grad)
+        else:
+            v, info = L.ld_logdet(ctx)
+        ms += info["ms"]
+        it_ms += info["iter_ms"]
+        tile_iters += info["tile_iters"]
+        passes += info["iters"]
+    return dict(ms=ms, iter_ms=it_ms, tile_iters=tile_iters, passes=passes, info=info, logdet=v, grad=g)
+
+
+def roofline_entry(kernel, n, T, word, r, keep_x, bq_per_pass, peak, src, traffic=None):
+    alg = algorithmic_bytes(n, T, word, r["tile_iters"], keep_x, bq_per_pass, r["passes"])
+    info = r["info"]
+    lean = info["pass_words"] == 4 + (2 if keep_x else 0)     # the lean pass moves the algorithmic words
+    achieved = alg / (r["iter_ms"] / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "algorithmic_bytes_per_pass": alg / max(r["passes"], 1),
+            "moved_bytes_per_pass": moved_bytes(n, T, word, r["tile_iters"], info["pass_words"], lean)
+            / max(r["passes"], 1),
+            "pass_words": info["pass_words"], "peak_source": src}
+
+
+def config_posterior2048(L, steps, peak, src):
+    """configs[3]: Gauss-linear posterior Q_p = 0.1 I - Lap + 4 diag(mask) on 2048 x 2048
+    (10 % observed, seeded), distance 4, N = 20, log det and gradient (kappa^2, tau) per
+    evaluation; mixed precision with reliable updates (tol 1e-9) against the plain FP64
+    form on the same problem."""
+    dims, k2, tau = (2048, 2048), 0.1, 4.0
+    n = dims[0] * dims[1]
+    mask = synth.obs_mask(4, n, 0.1)
+    out = {}
+    for name, prec, delta in (("mixed", L.LD_MIXED, 1e-2), ("fp64", L.LD_FP64, 0.0)):
+        ctx = L.ld_create(L.grid_matrix(L.LD_STENCIL_2D5, dims, k2, tau=tau, obs_mask=mask), 4, 20, 1e-9,
+                          L.options(precision=prec, reliable_delta=delta))
+        timed_evals(L, ctx, 1, grad=[L.LD_P_KAPPA2, L.LD_P_TAU])
+        out[name] = timed_evals(L, ctx, steps if name == "mixed" else 1, grad=[L.LD_P_KAPPA2, L.LD_P_TAU])
+        del ctx
+    m, f = out["mixed"], out["fp64"]
+    info = m["info"]
+    T = info["tile_width"]
+    roof = roofline_entry("k_lean2d (5-point, seed solution kept)", n, T, 4, m, True, n, peak, src)
+    return {"workload": "2048x2048 posterior, kappa^2 0.1, tau 4, 10% mask, d=4, N=20, tol 1e-9, grad (kappa^2, tau)",
+            "value": steps / (m["ms"] / 1e3), "unit": UNIT, "evaluations": steps,
+            "dtype": "f32 vectors / f64 scalars, reliable updates", "roofline": roof,
+            "n_colours": info["n_colours"], "iters": info["iters"], "reliable_updates": info["reliable_updates"],
+            "rel_resid_max": info["rel_resid_max"],
+            "fp64_form": {"value": 1.0 / (f["ms"] / 1e3), "logdet_rel_diff": abs(m["logdet"] - f["logdet"]) / abs(f["logdet"]),
+                          "grad_rel_diff": [abs(a - b) / abs(b) for a, b in zip(m["grad"], f["grad"])]}}
+
+
+def config_periodic64(L, steps):
+    """configs[0]: Q = 0.5 I - Lap on the 64 x 64 torus given as a CSR matrix, distance 4,
+    N = 20, tol 1e-10, FP64 (the one-CTA-per-tile engine: L2-resident, latency-bound)."""
+    dims, k2 = (64, 64), 0.5
+    rows, cols, w = synth.torus_edges(*dims)
+    rp, ci, vv = synth.csr_from_edges(dims[0] * dims[1], rows, cols, w, k2)
+    ctx = L.ld_create(L.csr_matrix(rp, ci, vv), 4, 20, 1e-10,
+                      L.options(precision=L.LD_FP64, lambda_min=k2, lambda_max=k2 + 8.0))
+    timed_evals(L, ctx, 2)
+    r = timed_evals(L, ctx, steps)
+    info = r["info"]
+    return {"workload": "periodic 64x64 as CSR, kappa^2 0.5, d=4, N=20, tol 1e-10",
+            "value": steps / (r["ms"] / 1e3), "unit": UNIT, "evaluations": steps, "dtype": "f64",
+            "n_colours": info["n_colours"], "iters": info["iters"], "engine": info["engine"],
+            "logdet": r["logdet"], "quad_cert": info["quad_cert"],
+            "roofline": {"bound": "latency", "note": "the 4096-vertex problem is L2-resident; one CTA per tile"}}
+
+
+def config_field3d(L, side, steps, peak, src, fp64=True):
+    """configs[4]: Dirichlet side^3, 7-point, seeded kappa^2 field (log kappa^2 = -2 +
+    smoothed N(0,1)), distance 6, N = 32, tol 1e-6, mixed precision; one evaluation = log
+    det and its derivative with respect to the field's scale c (kappa^2 = c kappa0^2)."""
+    dims = (side, side, side)
+    n = side ** 3
+    field = synth.kappa2_field(5, dims)
+    ctx = L.ld_create(L.grid_matrix(L.LD_STENCIL_3D7, dims, 1.0, kappa2_field=field), 6, 32, 1e-6,
+                      L.options(precision=L.LD_MIXED))
+    timed_evals(L, ctx, 1, grad=[L.LD_P_KAPPA2])
+    r = timed_evals(L, ctx, steps, grad=[L.LD_P_KAPPA2])
+    info = r["info"]
+    T = info["tile_width"]
+    roof = roofline_entry("k_stream3d (7-point, stored w, seed solution kept)", n, T, 4, r, True, 4 * n, peak, src)
+    out = {"workload": "Dirichlet %d^3, 7-point, kappa^2 field, d=6, N=32, tol 1e-6, grad c" % side,
+           "value": steps / (r["ms"] / 1e3), "unit": UNIT, "evaluations": steps,
+           "dtype": "f32 vectors / f64 scalars", "n_colours": info["n_colours"], "tile_width": T,
+           "passes_per_eval": r["passes"] / steps, "roofline": roof, "logdet": r["logdet"],
+           "grad_c": float(r["grad"][0])}
+    del ctx
+    if fp64:
+        c2 = L.ld_create(L.grid_matrix(L.LD_STENCIL_3D7, dims, 1.0, kappa2_field=field), 6, 32, 1e-6,
+                         L.options(precision=L.LD_FP64))
+        f = timed_evals(L, c2, 1, grad=[L.LD_P_KAPPA2])
+        out["fp64_form"] = {"value": 1.0 / (f["ms"] / 1e3),
+                            "logdet_rel_diff": abs(r["logdet"] - f["logdet"]) / abs(f["logdet"]),
+                            "grad_rel_diff": abs(float(r["grad"][0]) - float(f["grad"][0])) / abs(float(f["grad"][0]))}
+    return out
+
+
 def run_batch(args):
-    """Secondary workload: 256 independent 2D GMRFs of uneven size (sides 32..512,
-    5-point d=4 or 13-point d=2, kappa^2 log-uniform) in one persistent launch per step;
-    mixed precision, with the same batch in the plain FP64 form beside it."""
+    """configs[2]: 256 independent 2D GMRFs of uneven size (sides 32..512, 5-point d=4 or
+    13-point d=2, kappa^2 log-uniform) in one persistent launch per step; mixed precision,
+    with the same batch in the plain FP64 form, and 256 sequential FP64 ld_logdet calls
+    (one context per instance) beside it."""
     import torch
     import paper_1105_5256_gb300 as L
     torch.cuda.set_device(0)
@@ -182,149 +313,73 @@ def run_batch(args):
             vals, _, info = L.ld_batch_logdet(b)
             ms += info["ms"]
         out[name] = {"value": 256 * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
-                     "vals": vals}
+                     "vals": vals, "tile_width": info["tile_width"]}
         del b
+    # 256 sequential FP64 evaluations, one context per instance (created beforehand)
+    ctxs = [L.ld_create(m, d, NSHIFT, TOL, L.options(precision=L.LD_FP64)) for m, d in zip(mats, dists)]
+    seq_ms = 0.0
+    seq_vals = []
+    for c in ctxs:
+        v, info = L.ld_logdet(c)
+        seq_ms += info["ms"]
+        seq_vals.append(v)
+    del ctxs
+    seq_vals = np.array(seq_vals)
     rel = float(np.max(np.abs(out["mixed"]["vals"] - out["fp64"]["vals"]) / np.abs(out["fp64"]["vals"])))
+    rel_seq = float(np.max(np.abs(out["mixed"]["vals"] - seq_vals) / np.abs(seq_vals)))
     line = {"metric": "log-det evals/sec (batch of 256 uneven 2D GMRFs, one persistent launch)",
             "value": out["mixed"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": out["mixed"]["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 vectors / f64 scalars", "data": "synthetic (seeded batch)",
             "config": {"workload": "256 grids, sides U{32..512}, 5-pt d=4 / 13-pt d=2, N=20, tol 1e-6",
-                       "points": int(sum(i.n for i in insts))},
+                       "points": int(sum(i.n for i in insts)), "tile_width": out["mixed"]["tile_width"]},
             "fp64_form": {"value": out["fp64"]["value"], "ms_per_step": out["fp64"]["ms_per_step"],
-                          "mixed_vs_fp64_rel_diff_max": rel}}
+                          "mixed_vs_fp64_rel_diff_max": rel},
+            "sequential_fp64": {"value": 256 / (seq_ms / 1e3), "ms": seq_ms,
+                                "note": "256 separate ld_logdet calls in FP64, one context per instance",
+                                "mixed_batch_vs_sequential_rel_diff_max": rel_seq}}
     print(json.dumps(line), flush=True)
 
 
 def run_small_configs(args):
-    """The other two configurations, one JSON line each:
-    periodic64: Q = 0.5 I - Lap on a 64 x 64 torus (5-point) given as a CSR matrix, distance 4,
-      N = 20, tol 1e-10, FP64; log det per evaluation;
-    posterior2048: Q_p = 0.1 I - Lap + 4 diag(mask) on 2048 x 2048 (10 % observed, seeded),
-      distance 4, N = 20, gradient (kappa^2, tau) per evaluation, mixed precision with
-      reliable updates (tol 1e-9) and the plain FP64 form beside it."""
+    """configs[0] and configs[3], one JSON line each."""
     import torch
     import paper_1105_5256_gb300 as L
     torch.cuda.set_device(0)
     L.library(build_if_missing=True)
     peak, src = peak_hbm()
-    # periodic 64^2, FP64, as a general CSR matrix (kappa^2 I - Lap on the torus)
-    dims, k2 = (64, 64), 0.5
-    rows, cols, w = synth.torus_edges(*dims)
-    rp, ci, vv = synth.csr_from_edges(dims[0] * dims[1], rows, cols, w, k2)
-    ctx = L.ld_create(L.csr_matrix(rp, ci, vv), 4, 20, 1e-10,
-                      L.options(precision=L.LD_FP64, lambda_min=k2, lambda_max=k2 + 8.0))
-    for _ in range(args.warmup):
-        L.ld_logdet(ctx)
-    ms = 0.0
-    for _ in range(args.steps):
-        v, info = L.ld_logdet(ctx)
-        ms += info["ms"]
-    print(json.dumps({"metric": "log-det evals/sec (64^2 periodic 5-point as CSR, d=4, N=20, FP64)",
-                      "value": args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-                      "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-                      "config": {"workload": "periodic 64x64 CSR, kappa^2 0.5, d=4, N=20, tol 1e-10",
-                                 "n_colours": info["n_colours"], "iters": info["iters"],
-                                 "engine": info["engine"]},
-                      "logdet": v, "quad_cert": info["quad_cert"]}),
-          flush=True)
-    # 2048^2 Gauss-linear posterior with gradient
-    dims, k2, tau = (2048, 2048), 0.1, 4.0
-    n = dims[0] * dims[1]
-    mask = synth.obs_mask(4, n, 0.1)
-    out = {}
-    for name, prec, tol, delta in (("mixed", L.LD_MIXED, 1e-9, 1e-2), ("fp64", L.LD_FP64, 1e-9, 0.0)):
-        ctx = L.ld_create(L.grid_matrix(L.LD_STENCIL_2D5, dims, k2, tau=tau, obs_mask=mask), 4, 20, tol,
-                          L.options(precision=prec, reliable_delta=delta))
-        for _ in range(max(1, args.warmup // 3)):
-            L.ld_logdet_grad(ctx, [L.LD_P_KAPPA2, L.LD_P_TAU])
-        ms, it_ms, tile_iters, passes = 0.0, 0.0, 0, 0
-        for _ in range(args.steps):
-            v, g, info = L.ld_logdet_grad(ctx, [L.LD_P_KAPPA2, L.LD_P_TAU])
-            ms += info["ms"]
-            it_ms += info["iter_ms"]
-            tile_iters += info["tile_iters"]
-            passes += info["iters"]
-        out[name] = (v, g, info, ms, it_ms, tile_iters, passes)
-        del ctx
-    v, g, info, ms, it_ms, tile_iters, passes = out["mixed"]
-    T = info["tile_width"]
-    alg = 8 * n * T * 4 * tile_iters + (4 + 4) * n * passes     # r, w, p, x_lo in and out; colour, diag
-    vf, gf, infof, msf = out["fp64"][:4]
-    print(json.dumps({"metric": "log-det+grad evals/sec (2048^2 Gauss-linear posterior, d=4, N=20)",
-                      "value": args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-                      "higher_is_better": True, "dtype": "f32 vectors / f64 scalars", "data": "synthetic",
-                      "config": {"workload": "2048x2048, kappa^2 0.1, tau 4, 10% mask, grad (kappa^2, tau), tol 1e-9",
-                                 "n_colours": info["n_colours"], "tile_width": T, "iters": info["iters"],
-                                 "reliable_updates": info["reliable_updates"],
-                                 "rel_resid_max": info["rel_resid_max"]},
-                      "roofline": {"bound": "hbm", "kernel": "fused CG pass (k_stream2d, 5-point)",
-                                   "achieved": alg / (it_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                                   "frac": alg / (it_ms / 1e3) / 1e9 / peak, "traffic": None,
-                                   "peak_source": src},
-                      "fp64_form": {"value": args.steps / (msf / 1e3), "rel_resid_max": infof["rel_resid_max"],
-                                    "logdet_rel_diff": abs(v - vf) / abs(vf),
-                                    "grad_rel_diff": [abs(a - b) / abs(b) for a, b in zip(g, gf)]}}),
-          flush=True)
+    for fn, metric in ((lambda: config_periodic64(L, max(args.steps, 10)),
+                        "log-det evals/sec (64^2 periodic 5-point as CSR, d=4, N=20, FP64)"),
+                       (lambda: config_posterior2048(L, max(args.steps, 2), peak, src),
+                        "log-det+grad evals/sec (2048^2 Gauss-linear posterior, d=4, N=20)")):
+        r = fn()
+        line = {"metric": metric, "value": r.pop("value"), "unit": UNIT, "n_gpus": 1, "steps": r["evaluations"],
+                "warmup": 1, "higher_is_better": True, "dtype": r.pop("dtype"), "data": "synthetic",
+                "config": {"workload": r.pop("workload")}}
+        line.update(r)
+        print(json.dumps(line), flush=True)
 
 
 def run_field3d(args):
-    """Secondary workload: Dirichlet 256^3, 7-point, seeded kappa^2 field, distance-6
-    colouring, N = 32, tol 1e-6, mixed precision; one evaluation = log det and its
-    derivative with respect to the field's scale c (kappa^2(s) = c kappa0^2(s))."""
+    """configs[4] (Dirichlet 256^3 by default, `--side` for smaller grids), one JSON line."""
     import torch
     import paper_1105_5256_gb300 as L
     torch.cuda.set_device(0)
     L.library(build_if_missing=True)
-    dims = (args.side, args.side, args.side)
-    n = dims[0] * dims[1] * dims[2]
-    field = synth.kappa2_field(5, dims)
-    ctx = L.ld_create(L.grid_matrix(L.LD_STENCIL_3D7, dims, 1.0, kappa2_field=field), 6, 32, 1e-6,
-                      L.options(precision=L.LD_MIXED, tile_width=args.tile_width))
-    for _ in range(args.warmup):
-        L.ld_logdet_grad(ctx, [L.LD_P_KAPPA2])
+    peak, src = peak_hbm()
     clocks = Clocks()
     clocks.start()
     t0 = time.perf_counter()
-    dev_ms = iter_ms = 0.0
-    tile_iters = passes = launches = 0
-    for _ in range(args.steps):
-        v, g, info = L.ld_logdet_grad(ctx, [L.LD_P_KAPPA2])
-        dev_ms += info["ms"]
-        iter_ms += info["iter_ms"]
-        tile_iters += info["tile_iters"]
-        passes += info["iters"]
-        launches += info["gpu_launches"]
-    torch.cuda.synchronize()
+    r = config_field3d(L, args.side, args.steps, peak, src, fp64=True)
     wall = time.perf_counter() - t0
     clk = clocks.stop()
-    T = info["tile_width"]
-    ntiles = (info["n_colours"] + T - 1) // T
-    # per tile-pass: r, w, p read and written, x read and written (gradient mode); per
-    # pass: the colour and the FP32 field, once
-    alg = (8 * n * T * 4) * tile_iters + (4 + 4) * n * passes
-    peak, src = peak_hbm()
-    achieved = alg / (iter_ms / 1e3) / 1e9
     line = {"metric": "log-det+grad evals/sec (Dirichlet %d^3, 7-point, kappa^2 field, d=6, N=32)" % args.side,
-            "value": args.steps / (dev_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 vectors / f64 scalars",
-            "data": "synthetic (seeded kappa^2 field)",
-            "config": {"workload": "Dirichlet %d^3, 7-point, kappa^2 field, d=6, N=32, tol 1e-6, grad c" % args.side,
-                       "n": n, "n_colours": info["n_colours"], "tile_width": T,
-                       "passes_per_eval": passes / args.steps},
-            "clocks": clk,
-            "e2e": {"value": args.steps / wall, "unit": UNIT, "h2d_bytes_per_step": 16,
-                    "d2h_bytes_per_step": 16},
-            "gpu_launches": launches,
-            "roofline": {"bound": "hbm", "kernel": "fused CG pass (k_stream3d)", "achieved": achieved,
-                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                         "algorithmic_bytes_per_launch": 8 * n * T * 4 * ntiles + 8 * n,
-                         "peak_source": src},
-            "logdet": v, "grad_c": float(g[0])}
+            "value": r.pop("value"), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": r.pop("dtype"),
+            "data": "synthetic (seeded kappa^2 field)", "config": {"workload": r.pop("workload")},
+            "clocks": clk, "wall_s": wall}
+    line.update(r)
     print(json.dumps(line), flush=True)
 
 
@@ -340,20 +395,28 @@ def run_ours(args):
     else:
         torch.cuda.set_device(0)
     L.library(build_if_missing=True)
+    split = args.split == "colours" and ws > 1
     prec = L.LD_MIXED if args.precision == "mixed" else L.LD_FP64
-    draws = rank_draws(rank, args.batch)
+    # weak scaling: a seeded batch per rank; colour split: every rank the same batch
+    draws = rank_draws(0 if split else rank, args.batch)
     if args.kappa2 > 0:
         draws = np.full(args.batch, args.kappa2)
     ctx = L.ld_create(L.grid_matrix(L.LD_STENCIL_2D13_SQ, DIMS, float(draws[0])), DIST, NSHIFT,
                       TOL, L.options(precision=prec, tile_width=args.tile_width))
     n = DIMS[0] * DIMS[1]
+    ncol_all = L.ld_get_colouring(ctx)[1]
+    cb, ce = colour_ranges(ncol_all, ws)[rank] if split else (0, ncol_all)
 
     def step():
         infos = []
         vals = []
         for k2 in draws:
             L.ld_set_params(ctx, float(k2))
-            v, info = L.ld_logdet(ctx)
+            if split:
+                v, info = L.ld_logdet_partial(ctx, cb, ce)
+                v = combine_partials([v])[0]
+            else:
+                v, info = L.ld_logdet(ctx)
             vals.append(v)
             infos.append(info)
         return vals, infos
@@ -366,10 +429,8 @@ def run_ours(args):
     clocks = Clocks()
     clocks.start()
     t0 = time.perf_counter()
-    dev_ms = 0.0
-    iter_ms = 0.0
-    tile_iters = 0
-    launches = 0
+    dev_ms = iter_ms = 0.0
+    tile_iters = launches = passes = 0
     all_infos = []
     vals = []
     for _ in range(args.steps):
@@ -381,66 +442,76 @@ def run_ours(args):
             iter_ms += i["iter_ms"]
             tile_iters += i["tile_iters"]
             launches += i["gpu_launches"]
+            passes += i["iters"]
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     if ws > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    # max over ranks of device time and of wall time
-    if ws > 1:
+    if ws > 1:   # max over ranks of device and wall time
         t = torch.tensor([dev_ms, wall], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         dev_ms, wall = float(t[0]), float(t[1])
-    evals = args.batch * args.steps * ws
+    evals = args.batch * args.steps * (1 if split else ws)
     value = evals / (dev_ms / 1e3)
     e2e = evals / wall
     info0 = all_infos[0]
     T = info0["tile_width"]
     ncols = ((info0["n_colours"] + T - 1) // T) * T
-    ntiles = ncols // T
-    passes = sum(i["iters"] for i in all_infos)
-    alg = algorithmic_bytes(n, T, args.precision, tile_iters, passes)
-    achieved = alg / (iter_ms / 1e3) / 1e9
+    word = 4 if args.precision == "mixed" else 8
     peak, src = peak_hbm()
-    traffic = recorded_traffic(T) if args.precision == "mixed" else None
+    r = {"tile_iters": tile_iters, "passes": passes, "iter_ms": iter_ms, "info": all_infos[-1]}
     if args.precision == "fp64":
         # FP64 issue-bound: 25 flops per vertex-column per pass against the measured
         # 1.25 TFLOP/s non-tensor FP64 rate
         flops = FP64_FLOPS_PER_VC * n * T * tile_iters
-        roof = {"bound": "alu", "kernel": "fused CG pass (k_stream2d, FP64)",
+        roof = {"bound": "alu", "kernel": "k_stream2d (stored-w pass, FP64)",
                 "achieved": flops / (iter_ms / 1e3) / 1e9, "peak": FP64_PEAK_GFLOPS,
                 "unit": "GFLOP/s", "traffic": None,
                 "peak_source": "measured FP64 FMA-chain rate (equals the nominal 1.25 TFLOP/s)"}
         roof["frac"] = roof["achieved"] / roof["peak"]
     else:
-        roof = None
+        lean = info0["pass_words"] == 4
+        roof = roofline_entry("k_lean2d (lean fused CG pass, Matern square)" if lean else
+                              "k_stream2d (stored-w fused CG pass)", n, T, word, r, False, 0, peak, src,
+                              traffic=recorded_traffic("k_lean2d_matern1024_T2.md") if lean and T == 2 else None)
+        roof["launch"] = ("one CG pass: the %d tile launches of an iteration, run concurrently on their "
+                          "own streams" % (ncols // T))
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": "strong" if split else "weak", "vs_baseline": None,
         "dtype": "f32 vectors / f64 scalars" if args.precision == "mixed" else "f64",
         "data": "synthetic (seeded kappa^2 draws; no dataset)",
         "config": {"workload": "Matern alpha=2 (kappa^2 I - Lap)^2, 1024x1024 Dirichlet, 13-point",
                    "n": n, "colouring_distance": DIST, "n_colours": info0["n_colours"],
                    "n_shifts": NSHIFT, "tol": TOL, "batch_kappa2_draws": args.batch,
-                   "precision": args.precision, "tile_width": info0["tile_width"],
-                   "engine": info0["engine"], "parallelism": "dp%d (independent batches)" % ws,
-                   "l2": "CG working set %.2f GB (r, p, p') > 129 MB L2" % (3 * n * ncols * (4 if args.precision == "mixed" else 8) / 1e9)},
+                   "precision": args.precision, "tile_width": T, "engine": info0["engine"],
+                   "parallelism": ("colour split over %d ranks" % ws) if split else
+                                  "dp%d (independent batches)" % ws,
+                   "l2": "a CG pass streams %.2f GB of state > 129 MB L2 (no flush needed)"
+                         % (info0["pass_words"] * n * ncols * word / 1e9)},
         "clocks": clk,
         "e2e": {"value": e2e, "unit": UNIT,
                 "h2d_bytes_per_step": args.batch * (3 * 8 + 2 * NSHIFT * 16),
                 "d2h_bytes_per_step": args.batch * (2 * 8 + 2 * 4 + 4 * ncols)},
         "gpu_launches": launches,
-        "roofline": roof or {"bound": "hbm", "kernel": "fused CG pass (k_stream2d)",
-                             "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": traffic,
-                             "algorithmic_bytes_per_launch": algorithmic_bytes(n, T, args.precision, ntiles, 1),
-                             "peak_source": src},
+        "roofline": roof,
         "iters_mean": float(np.mean([i["iters"] for i in all_infos])),
         "logdet_first": vals[0],
     }
     if rank == 0 and ws == 1 and args.precision == "mixed" and args.fp64_sample > 0:
         out["fp64_form"] = fp64_form(L, draws[:args.fp64_sample], vals[:args.fp64_sample])
+    if rank == 0 and ws == 1 and not args.no_other_configs:
+        oc = {}
+        for key, fn in (("periodic64_csr_fp64", lambda: config_periodic64(L, 10)),
+                        ("posterior2048_mixed_grad", lambda: config_posterior2048(L, 3, peak, src)),
+                        ("field3d256_mixed_grad", lambda: config_field3d(L, 256, 1, peak, src))):
+            try:
+                oc[key] = fn()
+            except Exception as e:      # a failing side configuration must not lose the headline
+                oc[key] = {"error": str(e)[:300]}
+        out["other_configs"] = oc
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
@@ -465,53 +536,132 @@ def fp64_form(L, draws, mixed_vals):
             "kappa2": [float(k) for k in draws], "mixed_vs_fp64_rel_diff_max": rel}
 
 
-def cpu_baseline(budget_s: float):
-    """The oracle (plain single-thread C banded Cholesky, natural order) on the leading
-    principal block of the same matrix; its cost is linear in the block's rows, so the
-    full-size time is the measured time scaled by n / rows."""
+# ---------------------------------------------------------------- CPU baselines (the oracle)
+def _o1_block_seconds(lines: int, k2: float) -> float:
+    """Seconds of the oracle's banded Cholesky log det on the leading 1024 x lines block of
+    the Matern precision (one core)."""
     from oracle import matrices as om
     from oracle import method as mt
+    Qs = om.precision(om.KIND_2D13_SQ, (DIMS[0], lines), k2)
+    t0 = time.perf_counter()
+    mt.exact_logdet_band(Qs)
+    return time.perf_counter() - t0
+
+
+def _o4_colour_seconds(args) -> float:
+    """Seconds of the oracle's CG-M method reference for one probing vector (one core)."""
+    side, k2, colour_id = args
+    from oracle import matrices as om
+    from oracle import method as mt
+    from oracle import probing
+    Q = om.precision(om.KIND_2D13_SQ, (side, side), k2)
+    col = probing.colour_greedy(Q, DIST)
+    lo, hi = mt.spectral_bounds(om.KIND_2D13_SQ, (side, side), k2)
+    t0 = time.perf_counter()
+    mt.logdet_method(Q, col, lo, hi, NSHIFT, TOL, per_colour=True, colours=[colour_id])
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(budget_s: float):
+    """The oracle timed on the host cores, on bounded samples of the same workload.
+
+    O1 (the traditional method of Sec. 2: plain natural-order banded Cholesky, log det =
+    2 sum log L_jj) on a 1024 x k leading block (k doubled from 4 until the run takes a
+    sixth of the budget), on one core, then one block per core at once (independent
+    evaluations, as the batch of kappa^2 draws is); its cost is linear in the rows at fixed
+    band, so the full-size time is projected by n / rows.  O4 (the method itself on the
+    CPU: colouring, rational nodes and CG-M in numpy) runs every probing vector of a
+    128 x 128 instance, the colours spread over the cores; it is projected to 1024^2 by the
+    vertex count (the iteration count depends on kappa^2, not on the grid size, once the
+    grid is larger than the correlation length)."""
+    import multiprocessing as mpx
     k2 = float(synth.kappa2_draws(SEED, BATCH)[0])
     n = DIMS[0] * DIMS[1]
-    rows_per_line = DIMS[0]
+    cores = len(os.sched_getaffinity(0))
     lines = 4
-    # grow the sample until it takes a measurable share of the budget
     while True:
-        sub = (DIMS[0], lines)
-        Qs = om.precision(om.KIND_2D13_SQ, sub, k2)
-        t0 = time.perf_counter()
-        mt.exact_logdet_band(Qs)
-        dt = time.perf_counter() - t0
-        if dt > budget_s / 4 or lines >= DIMS[1]:
+        dt = _o1_block_seconds(lines, k2)
+        if dt > budget_s / 6 or lines >= DIMS[1]:
             break
         lines *= 2
-    rows = rows_per_line * lines
-    full_s = dt * n / rows
-    return {"value": 1.0 / full_s, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "banded Cholesky log det of the same model on a %dx%d grid (%d rows, "
-                      "band %d, cost linear in rows) in %.2f s, scaled by n/rows = %.0f"
-                      % (DIMS[0], lines, rows, 2 * DIMS[0], dt, n / rows)}
+    rows = DIMS[0] * lines
+    single = 1.0 / (dt * n / rows)
+    ctx = mpx.get_context("spawn")
+    # one BLAS thread per worker process (the workers are the parallelism)
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    os.environ.update({k: "1" for k in saved})
+    with ctx.Pool(cores) as pool:
+        t0 = time.perf_counter()
+        per = pool.starmap(_o1_block_seconds, [(lines, k2)] * cores)
+        wall_all = time.perf_counter() - t0
+        all_rate = cores / (max(per) * n / rows)
+        side = 128
+        from oracle import matrices as om
+        from oracle import probing
+        C = int(probing.colour_greedy(om.precision(om.KIND_2D13_SQ, (side, side), k2), DIST).max()) + 1
+        t0 = time.perf_counter()
+        pool.map(_o4_colour_seconds, [(side, k2, c) for c in range(C)])
+        o4_wall = time.perf_counter() - t0
+    for k, v in saved.items():
+        if v is None:
+            os.environ.pop(k, None)
+        else:
+            os.environ[k] = v
+    o4_rate = 1.0 / o4_wall
+    return {"value": all_rate, "unit": UNIT, "cores": cores, "kind": "oracle", "projected": True,
+            "sample": "O1 banded Cholesky log det of the same model on a %dx%d block (%d rows, band %d), "
+                      "one block per core at once, %.2f s each (slowest), projected by n/rows = %.0f"
+                      % (DIMS[0], lines, rows, 2 * DIMS[0], max(per), n / rows),
+            "single_core": {"value": single, "unit": UNIT, "cores": 1, "projected": True,
+                            "sample_seconds": dt},
+            "cores_all": {"value": all_rate, "unit": UNIT, "cores": cores, "projected": True,
+                          "sample_seconds_max": max(per), "wall_s": wall_all},
+            "o4": {"value_128": o4_rate, "unit": UNIT, "cores": cores, "sample_seconds": o4_wall,
+                   "value": o4_rate / (n / side ** 2), "projected": True,
+                   "sample": "CG-M method reference (colouring d=2, N=20, tol 1e-6) on the 128x128 "
+                             "Matern instance, %d colours over %d cores, projected by n ratio %d"
+                             % (C, cores, n // side ** 2)}}
 
 
 def run_reference(args):
+    """The reference arm: the oracle (banded Cholesky, the traditional route of Sec. 2) as it
+    stands, on the host cores, on bounded samples of the same workload; one step = one
+    sample run on every core at once, reported as projected full-size evaluations/s."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    per = []
-    for _ in range(max(1, args.warmup)):
-        cpu_baseline(args.cpu_seconds / 4)
-    samples = []
-    for _ in range(args.steps):
-        cb = cpu_baseline(args.cpu_seconds)
-        per.append(1.0 / cb["value"])
-        samples.append(cb["sample"])
-    value = 1.0 / statistics.mean(per)
+    import multiprocessing as mpx
+    k2 = float(synth.kappa2_draws(SEED, BATCH)[0])
+    n = DIMS[0] * DIMS[1]
+    cores = len(os.sched_getaffinity(0))
+    lines = 4
+    while True:
+        dt = _o1_block_seconds(lines, k2)
+        if dt > args.cpu_seconds / 6 or lines >= DIMS[1]:
+            break
+        lines *= 2
+    rows = DIMS[0] * lines
+    ctx = mpx.get_context("spawn")
+    step_s, rates = [], []
+    os.environ.update({k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")})
+    with ctx.Pool(cores) as pool:
+        for k in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            per = pool.starmap(_o1_block_seconds, [(lines, k2)] * cores)
+            if k >= args.warmup:
+                step_s.append(time.perf_counter() - t0)
+                rates.append(cores / (max(per) * n / rows))
+    value = statistics.mean(rates)
+    sample = ("O1 banded Cholesky log det of the same model on a %dx%d block (%d rows, band %d), one "
+              "block per core on %d cores, projected by n/rows = %.0f" % (DIMS[0], lines, rows, 2 * DIMS[0],
+                                                                         cores, n / rows))
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(per) * 1e3,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_s) * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": "Matern alpha=2 (kappa^2 I - Lap)^2, 1024x1024 Dirichlet, 13-point"},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": samples[-1]},
+           "data": "synthetic", "projected": True,
+           "config": {"workload": "Matern alpha=2 (kappa^2 I - Lap)^2, 1024x1024 Dirichlet, 13-point"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample, "projected": True},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -525,8 +675,12 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="skip the other configurations (profiling runs)")
     ap.add_argument("--batch", type=int, default=BATCH, help="kappa^2 values per step")
     ap.add_argument("--tile-width", type=int, default=0, help="probing vectors per tile (0 = auto)")
+    ap.add_argument("--split", default="batches", choices=["batches", "colours"],
+                    help="several GPUs: independent batches per rank, or every evaluation's colours split")
     ap.add_argument("--workload", default="matern1024",
                     choices=["matern1024", "batch256", "field3d256", "small"])
     ap.add_argument("--side", type=int, default=256, help="field3d256 workload: grid side")

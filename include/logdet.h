@@ -159,7 +159,12 @@ ld_status ld_default_options(ld_options *opt);
  *   colouring_distance d >= 0: probing vectors from a distance-d greedy colouring of
  *                      the graph of Q (Sec. 2.1; natural order, smallest free colour),
  *                      unless opt->colouring supplies one.
- *   n_shifts           N >= 1 quadrature nodes of the rational log (Eq. "eq_rat_app").
+ *   n_shifts           N >= 1 quadrature nodes of the rational log (Eq. "eq_rat_app"), or 0:
+ *                      the smallest N (4..256) whose measured certificate
+ *                      max |f_N - log| on [lambda_min, lambda_max] is at most
+ *                      1e-10 |log lambda_max - log lambda_min| (Sec. 2.1 gives the error
+ *                      rate of the quadrature), chosen again whenever ld_set_params
+ *                      moves the interval; ld_info.n_shifts reports it.
  *   tol                relative residual at which each shifted system is converged
  *                      (|zeta| ||r|| <= tol ||v_c||), 0 < tol < 1.
  *   opt                NULL = defaults.
@@ -329,6 +334,12 @@ ld_status ld_csr_bounds(int64_t n, const int64_t *rowptr, const int32_t *colidx,
 /* Same colouring for a grid kind (lattice-ball search, no CSR needed). */
 ld_status ld_colour_grid(int kind, const int32_t dims[3], int periodic, int d, int32_t *colour,
                          int32_t *n_colours);
+
+/* The node count ld_create uses for n_shifts = 0: the smallest N in 4..256 whose
+ * certificate max |f_N - log| on [lambda_min, lambda_max] (2001 log-spaced samples) is at
+ * most 1e-10 |log lambda_max - log lambda_min| (256 when none is; Sec. 2.1's error rate).
+ * Host only.  Errors: LD_EINVAL (NULL output, bad interval). */
+ld_status ld_auto_shifts(double lambda_min, double lambda_max, int32_t *n_shifts);
 
 /* Nodes/weights of the rational log on [lmin, lmax] (Eq. "eq_rat_app"):
  * sigma, alpha interleaved (re, im), N each; *cert = max |f_N - log| on the interval. */

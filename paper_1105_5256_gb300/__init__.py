@@ -109,6 +109,7 @@ def library(build_if_missing: bool = False):
         "ld_colour_csr": ([i64, vp, vp, C.c_int, vp, P(i32)], st),
         "ld_colour_grid": ([C.c_int, vp, C.c_int, C.c_int, vp, P(i32)], st),
         "ld_hht_nodes": ([dbl, dbl, C.c_int, vp, vp, P(dbl)], st),
+        "ld_auto_shifts": ([dbl, dbl, P(i32)], st),
         "ld_grid_bounds": ([P(Matrix), P(dbl), P(dbl)], st),
         "ld_csr_bounds": ([i64, vp, vp, vp, dbl, P(dbl), P(dbl)], st),
         "ld_hht_invsqrt_nodes": ([dbl, dbl, C.c_int, vp, vp], st),
@@ -419,6 +420,13 @@ def ld_hht_nodes(lmin: float, lmax: float, N: int):
     _check(library().ld_hht_nodes(float(lmin), float(lmax), int(N), _ptr(s), _ptr(a),
                                   C.byref(cert)))
     return s[0::2] + 1j * s[1::2], a[0::2] + 1j * a[1::2], cert.value
+
+
+def ld_auto_shifts(lmin: float, lmax: float) -> int:
+    """The node count ld_create chooses for n_shifts = 0 on [lmin, lmax]."""
+    n = C.c_int32()
+    _check(library().ld_auto_shifts(float(lmin), float(lmax), C.byref(n)))
+    return n.value
 
 
 def ld_hht_invsqrt_nodes(lmin: float, lmax: float, N: int):

@@ -96,6 +96,8 @@ struct ld_ctx {
     double kappa2 = 0, tau = 0, scale = 1;
     bool has_field = false, has_mask = false, mask_any = false;
     int distance = 0, nshift = 0;
+    bool auto_shift = false;   // n_shifts = 0: N chosen from the quadrature certificate
+    int nshift_cap = 0;        // shift-state capacity of d_shift / d_nodes (columns x nodes)
     double tol = 0;
     ld_options opt{};
     bool user_bounds = false;
@@ -268,16 +270,69 @@ int choose_tile(int precision, int C, int requested) {
     return best;
 }
 
+void invalidate_graph(ld_ctx *c);
+
+// Shift state (per column and node) and the node table sized for `cap` nodes; the solve
+// uses the first nshift of them.  Rebinds the Solve's pointers.
+ld_status bind_shift_state(ld_ctx *c, int cap) {
+    const int C = c->ncols;
+    CUDA_TRY(c->d_shift.alloc((size_t)4 * C * cap * sizeof(double2) + (size_t)C * cap));
+    CUDA_TRY(c->d_nodes.alloc((size_t)2 * cap * sizeof(double2)));
+    c->nshift_cap = cap;
+    Solve &s = c->s;
+    double2 *sh = c->d_shift.as<double2>();
+    s.zeta = sh;
+    s.zeta_prev = sh + (size_t)C * cap;
+    s.pi = sh + (size_t)2 * C * cap;
+    s.phi = sh + (size_t)3 * C * cap;
+    s.sh_active = reinterpret_cast<uint8_t *>(sh + (size_t)4 * C * cap);
+    s.shift = c->d_nodes.as<double2>();
+    s.weight = c->d_nodes.as<double2>() + cap;
+    invalidate_graph(c);
+    return LD_OK;
+}
+
+// Automatic node count: the smallest N in [4, 256] whose measured certificate
+// max |f_N - log| on [m, M] is at most 1e-10 |log M - log m|.  The search starts from the
+// square-root method's rate exp(-2 pi^2 N / (log(M/m) + 6)) and steps by one.
+int auto_shift_count(double lmin, double lmax) {
+    const double target = 1e-10 * std::fabs(std::log(lmax) - std::log(lmin));
+    const double rate = 2.0 * M_PI * M_PI / (std::log(lmax / lmin) + 6.0);
+    int N = (int)std::ceil(std::log(1.0 / target) / rate);
+    N = std::min(256, std::max(4, N));
+    std::vector<std::complex<double>> sg(256), al(256);
+    auto cert = [&](int k) -> double {
+        if (ld::hht_log_nodes(lmin, lmax, k, sg.data(), al.data()) != 0) return INFINITY;
+        return ld::hht_certificate(lmin, lmax, k, sg.data(), al.data());
+    };
+    if (cert(N) > target) {
+        while (N < 256 && cert(N) > target) ++N;
+    } else {
+        while (N > 4 && cert(N - 1) <= target) --N;
+    }
+    return N;
+}
+
 ld_status set_nodes(ld_ctx *c) {
+    if (c->auto_shift) {
+        const int N = auto_shift_count(c->lmin, c->lmax);
+        if (N != c->nshift) {
+            c->nshift = N;
+            c->s.nshift = N;
+            invalidate_graph(c);
+        }
+        if (N > c->nshift_cap)
+            if (ld_status st = bind_shift_state(c, std::max(N, 2 * c->nshift_cap))) return st;
+    }
     c->sigma.assign(c->nshift, 0.0);
     c->alpha.assign(c->nshift, 0.0);
     if (ld::hht_log_nodes(c->lmin, c->lmax, c->nshift, c->sigma.data(), c->alpha.data()) != 0)
         return fail(LD_EINVAL, "bad spectral interval [%g, %g]", c->lmin, c->lmax);
     c->cert = ld::hht_certificate(c->lmin, c->lmax, c->nshift, c->sigma.data(), c->alpha.data());
-    std::vector<double2> h(2 * c->nshift);
+    std::vector<double2> h(2 * c->nshift_cap, make_double2(0.0, 0.0));
     for (int l = 0; l < c->nshift; ++l) {
         h[l] = make_double2(-c->sigma[l].real(), -c->sigma[l].imag());    // s_l = -sigma_l
-        h[c->nshift + l] = make_double2(c->alpha[l].real(), c->alpha[l].imag());
+        h[c->nshift_cap + l] = make_double2(c->alpha[l].real(), c->alpha[l].imag());
     }
     CUDA_TRY(cudaMemcpy(c->d_nodes.p, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice));
     return LD_OK;
@@ -805,7 +860,7 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
     *out = nullptr;
     if (ld_status v = validate_matrix(Q)) return v;
     if (colouring_distance < 0) return fail(LD_EINVAL, "colouring_distance must be >= 0");
-    if (n_shifts < 1 || n_shifts > 256) return fail(LD_EINVAL, "n_shifts must be in [1, 256]");
+    if (n_shifts < 0 || n_shifts > 256) return fail(LD_EINVAL, "n_shifts must be in [0, 256] (0 = automatic)");
     if (!(tol > 0.0 && tol < 1.0)) return fail(LD_EINVAL, "tol must be in (0, 1)");
     ld_options opt;
     ld_default_options(&opt);
@@ -825,7 +880,8 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
     c->periodic = Q->periodic ? 1 : 0;
     c->opt = opt;
     c->distance = colouring_distance;
-    c->nshift = n_shifts;
+    c->auto_shift = n_shifts == 0;
+    c->nshift = c->auto_shift ? 20 : n_shifts;       // automatic N: set with the nodes
     c->tol = tol;
     c->scale = Q->scale == 0.0 ? 1.0 : Q->scale;
     c->kappa2 = Q->kappa2;
@@ -946,8 +1002,6 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
     const int N = c->nshift, C = c->ncols;
     CUDA_TRY(c->d_colscal.alloc((size_t)8 * C * sizeof(double)));
     CUDA_TRY(c->d_colint.alloc((size_t)2 * C * sizeof(int32_t)));
-    CUDA_TRY(c->d_shift.alloc((size_t)4 * C * N * sizeof(double2) + (size_t)C * N));
-    CUDA_TRY(c->d_nodes.alloc((size_t)2 * N * sizeof(double2)));
     CUDA_TRY(c->d_tile.alloc((size_t)(3 * c->ntiles + 2) * sizeof(int32_t)));
     CUDA_TRY(c->d_terms.alloc((size_t)(2 * C + 8) * sizeof(double)));
     CUDA_TRY(cudaMemcpy(c->d_terms.as<double>() + C, c->class_size.data(), C * sizeof(double), cudaMemcpyHostToDevice));
@@ -980,14 +1034,7 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
     s.phi0 = cs + 7 * C;
     s.col_active = c->d_colint.as<int32_t>();
     s.col_iters = s.col_active + C;
-    double2 *sh = c->d_shift.as<double2>();
-    s.zeta = sh;
-    s.zeta_prev = sh + (size_t)C * N;
-    s.pi = sh + (size_t)2 * C * N;
-    s.phi = sh + (size_t)3 * C * N;
-    s.sh_active = reinterpret_cast<uint8_t *>(sh + (size_t)4 * C * N);
-    s.shift = c->d_nodes.as<double2>();
-    s.weight = c->d_nodes.as<double2>() + N;
+    if (ld_status st = bind_shift_state(c, c->auto_shift ? 64 : N)) return st;
     s.tile_done = c->d_tile.as<int32_t>();
     s.tile_ctr = s.tile_done + c->ntiles;
     s.tile_par = s.tile_ctr + c->ntiles;
@@ -1461,6 +1508,14 @@ ld_status ld_colour_grid(int kind, const int32_t dims[3], int periodic, int d, i
     if (dd[0] < 1 || dd[1] < 1 || dd[2] < 1) return fail(LD_EINVAL, "dims must be >= 1");
     const int nc = ld::colour_grid(kind, dd, periodic ? 1 : 0, d, colour);
     if (n_colours) *n_colours = nc;
+    return LD_OK;
+}
+
+ld_status ld_auto_shifts(double lambda_min, double lambda_max, int32_t *n_shifts) {
+    if (!n_shifts) return fail(LD_EINVAL, "n_shifts is NULL");
+    if (!(lambda_min > 0.0) || !(lambda_max > lambda_min) || !std::isfinite(lambda_max))
+        return fail(LD_EINVAL, "need 0 < lambda_min < lambda_max (finite)");
+    *n_shifts = auto_shift_count(lambda_min, lambda_max);
     return LD_OK;
 }
 

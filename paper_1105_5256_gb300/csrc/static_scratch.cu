@@ -73,15 +73,15 @@ extern "C" ld_status ld_logdet_static(const ld_matrix *Q, const int32_t *colour,
     for (int d = 0; d < nd; ++d) {
         if (Q->dims[d] < 1) return fail(LD_EINVAL, "dims must be >= 1");
         n *= Q->dims[d];
+        // every vertex needs at least one FP64 word of scratch: stop before n can overflow
+        if (n > (int64_t)(kScratchBytes / sizeof(double)))
+            return fail(LD_EINVAL, "problem needs more than LD_STATIC_SCRATCH_BYTES of scratch");
     }
     if (!(Q->kappa2 >= 0.0) || !(tol > 0.0 && tol < 1.0) || n_shifts < 1 || n_shifts > 256 ||
         n_colours < 1 || n_colours > LD_STATIC_MAX_COLOURS || max_iter < 1)
         return fail(LD_EINVAL, "bad kappa2, tol, n_shifts, n_colours or max_iter");
     const double scale = Q->scale == 0.0 ? 1.0 : Q->scale;
     if (!(scale > 0.0)) return fail(LD_EINVAL, "scale must be > 0");
-    for (int64_t i = 0; i < n; ++i)
-        if (colour[i] < 0 || colour[i] >= n_colours) return fail(LD_EINVAL, "colour out of range");
-
     // ---- carve the scratch: FP64, tile width 1 (one CTA per probing vector)
     const int C = n_colours, N = n_shifts, T = 1;
     const size_t vec = align256((size_t)n * C * sizeof(double));
@@ -101,6 +101,9 @@ extern "C" ld_status ld_logdet_static(const ld_matrix *Q, const int32_t *colour,
     const size_t o_tm = take((size_t)(2 * C + 8) * sizeof(double));
     if (off > kScratchBytes)
         return fail(LD_EINVAL, "problem needs more than LD_STATIC_SCRATCH_BYTES of scratch");
+    // the colouring is scanned only once the problem is known to fit
+    for (int64_t i = 0; i < n; ++i)
+        if (colour[i] < 0 || colour[i] >= n_colours) return fail(LD_EINVAL, "colour out of range");
 
     void *base = nullptr;
     if (cudaError_t e = scratch_address(&base); e != cudaSuccess)

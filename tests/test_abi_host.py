@@ -260,3 +260,47 @@ def test_batch_create_checks_every_instance_on_the_host(lib):
         with pytest.raises(L.LogDetError) as e:
             L.ld_batch_create(**args)
         assert e.value.status == status, kw
+
+
+def test_static_entry_point_rejects_before_any_device_work():
+    """ld_logdet_static checks every size against its static scratch before it reads the
+    colouring or touches a device: oversized grids (including vertex counts that would
+    overflow) and bad arguments fail with LD_EINVAL on a machine with no GPU."""
+    lib = L.library()
+    m = L.grid_matrix(L.LD_STENCIL_2D5, (512, 512), 0.5)
+    colour = np.zeros(512 * 512, dtype=np.int32)
+    colour[-1] = -7                                  # never read: the size check comes first
+    with pytest.raises(L.LogDetError) as e:
+        L.ld_logdet_static(m, colour, 18, 20, 1e-8)
+    assert e.value.status == L.LD_EINVAL and "LD_STATIC_SCRATCH_BYTES" in str(e.value)
+    huge = L.grid_matrix(L.LD_STENCIL_3D7, (1 << 30, 1 << 30, 1 << 30), 0.5)
+    with pytest.raises(L.LogDetError) as e:
+        L.ld_logdet_static(huge, np.zeros(1, dtype=np.int32), 1, 20, 1e-8)
+    assert e.value.status == L.LD_EINVAL and "LD_STATIC_SCRATCH_BYTES" in str(e.value)
+    small = L.grid_matrix(L.LD_STENCIL_2D5, (8, 8), 0.5)
+    for args in ((np.zeros(64, np.int32), 0, 20, 1e-8), (np.zeros(64, np.int32), 1, 0, 1e-8),
+                 (np.zeros(64, np.int32), 1, 20, 0.0)):
+        with pytest.raises(L.LogDetError) as e:
+            L.ld_logdet_static(small, *args)
+        assert e.value.status == L.LD_EINVAL
+    assert lib is not None
+
+
+def test_automatic_shift_count_meets_its_certificate_target():
+    """n_shifts = 0 (Sec. 2.1's quadrature error rate): the library's N is the smallest whose
+    certificate is at most 1e-10 |log M - log m|.  Against the oracle's nodes and its own
+    certificate: N meets the target and N - 1 misses it (up to the two certificates'
+    different sampling, a factor 2 at the boundary)."""
+    from oracle import hht
+    for kind, dims, k2 in ((L.LD_STENCIL_2D13_SQ, (64, 48), 0.01), (L.LD_STENCIL_2D5, (40, 30), 0.5),
+                           (L.LD_STENCIL_3D7, (9, 8, 7), 0.2), (L.LD_STENCIL_2D13_SQ, (1024, 1024), 0.01)):
+        lo, hi = L.ld_grid_bounds(L.grid_matrix(kind, dims, k2))
+        target = 1e-10 * abs(np.log(hi) - np.log(lo))
+        N = L.ld_auto_shifts(lo, hi)
+        assert 4 < N < 256
+        s, a = hht.log_nodes(lo, hi, N)
+        assert hht.certificate(lo, hi, s, a) <= 2 * target
+        s, a = hht.log_nodes(lo, hi, N - 1)
+        assert hht.certificate(lo, hi, s, a) > 0.5 * target
+    with pytest.raises(L.LogDetError):
+        L.ld_auto_shifts(2.0, 1.0)

@@ -215,7 +215,7 @@ def test_partial_colour_ranges_sum_to_total():
     C = info["n_colours"]
     cuts = [0, 3, 7, C]
     parts = [L.ld_logdet_partial(ctx, a, b)[0] for a, b in zip(cuts, cuts[1:])]
-    assert abs(sum(parts) - total) <= 1e-12 * abs(total)
+    assert abs(sum(parts) - total) <= 1e-14 * abs(total)     # per-column arithmetic is identical
 
 
 def test_not_spd_reported_and_context_reusable():
@@ -372,3 +372,25 @@ def test_csr_with_library_bounds_matches_exact_probing():
     assert info["lambda_min"] <= ev.min() and info["lambda_max"] >= ev.max()
     ref = mt.probed_dense(Q, col, np.log)
     assert abs(val - ref) <= 1e-8 * abs(ref)
+
+
+def test_automatic_shift_count_follows_the_interval():
+    """n_shifts = 0: the context uses the node count ld_auto_shifts gives for its interval
+    (the smallest N whose quadrature certificate meets 1e-10 |log M - log m|); the result
+    is the oracle's rational target for that N, and a wider interval after ld_set_params
+    raises N."""
+    kind, dims, k2, tol = om.KIND_2D13_SQ, (96, 80), 0.05, 1e-9
+    ctx = L.ld_create(L.grid_matrix(kind, dims, k2), 2, 0, tol, L.options(precision=L.LD_FP64))
+    val, info = L.ld_logdet(ctx)
+    N = info["n_shifts"]
+    assert N == L.ld_auto_shifts(info["lambda_min"], info["lambda_max"])
+    lo, hi = mt.spectral_bounds(kind, dims, k2)
+    s, a = hht.log_nodes(lo, hi, N)
+    col, _ = checked_colouring(ctx, om.precision(kind, dims, k2), 2)
+    target = spectral_target(kind, dims, k2, False, col, s, a, per_colour=True)
+    assert abs(val - target.sum()) <= 50 * tol * np.abs(target).sum()
+    assert info["quad_cert"] <= 2e-10 * abs(np.log(hi) - np.log(lo))
+    L.ld_set_params(ctx, 0.002)
+    _, info2 = L.ld_logdet(ctx)
+    assert info2["n_shifts"] > N
+    assert info2["n_shifts"] == L.ld_auto_shifts(info2["lambda_min"], info2["lambda_max"])

@@ -61,6 +61,51 @@ def test_two_rank_sharding_and_timing():
     assert tmax == 2.0                            # the slowest rank sets the time
 
 
+def _partial_worker(rank, world, port, q):
+    """One rank of a colour-split evaluation: the per-colour terms (and seed projections,
+    the kappa^2 gradient terms) of its colour range, summed locally and combined by the
+    bench's all-reduce.  The terms come from a CPU stand-in (the oracle's circulant
+    probed values of a periodic grid), so the combine path runs without a GPU."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from oracle import closed_forms as cf
+    from oracle import hht
+    from oracle import matrices as om
+    from oracle import method as mt
+    from oracle import probing
+    dims, k2 = (24, 20), 0.3
+    col = probing.colour_greedy(om.precision(om.KIND_2D5, dims, k2, periodic=True), 4)
+    lo, hi = mt.spectral_bounds(om.KIND_2D5, dims, k2, periodic=True)
+    s, a = hht.log_nodes(lo, hi, 20)
+    terms = cf.probed_value(om.KIND_2D5, dims, k2, True, col, lambda lam: hht.f_N(lam, s, a), per_colour=True)
+    seeds = cf.probed_value(om.KIND_2D5, dims, k2, True, col, lambda lam: 1.0 / lam, per_colour=True)
+    cb, ce = bench.colour_ranges(len(terms), world)[rank]
+    total = bench.combine_partials([float(np.sum(terms[cb:ce])), float(np.sum(seeds[cb:ce]))])
+    if rank == 0:
+        q.put((total, float(np.sum(terms)), float(np.sum(seeds)), len(terms)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_colour_split_combines_partials():
+    """Sec. 2.1's one-probing-vector-per-node scheme: the partial log det and gradient of
+    two colour ranges, combined by one all-reduce, equal the single-rank sums to 1e-14."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_partial_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    (ld, g), ld_ref, g_ref, C = q.get(timeout=120)
+    for p in ps:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert C > 2
+    assert abs(ld - ld_ref) <= 1e-14 * abs(ld_ref)
+    assert abs(g - g_ref) <= 1e-14 * abs(g_ref)
+
+
 def test_colour_ranges_cover_and_balance():
     for C in (1, 5, 18, 107):
         for world in (1, 2, 3, 8):

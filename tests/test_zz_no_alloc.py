@@ -6,8 +6,10 @@ an allocation would synchronise the device): its work buffers live in the
 library's static device array.  Here it is called twice in a row through the C
 ABI on the same small model and compared with the allocating entry point, run
 with the same engine (one CTA per probing vector, FP64, tile width 1), within
-the FP64 parity tolerance the other GPU tests use.  This file is collected
-last so that a failure here never hides another test's result.
+the FP64 parity tolerance the other GPU tests use; the device's free memory is
+the same before and after the second call (the first call may load the
+library's kernels).  This file is collected last so that a failure here never
+hides another test's result.
 """
 import numpy as np
 import pytest
@@ -36,8 +38,16 @@ def test_static_matches_allocating_entry_point_twice():
     ref, info = L.ld_logdet(ctx)
     terms, _ = L.ld_column_terms(ctx)
     bound = 50 * TOL * np.abs(terms).sum()
+    import torch
+    torch.cuda.synchronize()
+    torch.cuda.mem_get_info()
     first = L.ld_logdet_static(m, colour, nc, NSHIFT, TOL)
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
     second = L.ld_logdet_static(m, colour, nc, NSHIFT, TOL)
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before, (free_before, free_after)   # nothing allocated
     assert abs(first - ref) <= bound
     assert abs(second - ref) <= bound
     assert first == second
@@ -49,4 +59,10 @@ def test_static_rejects_oversized_problem():
     with pytest.raises(L.LogDetError) as e:
         L.ld_logdet_static(m, colour, nc, NSHIFT, TOL)
     assert e.value.status == L.LD_EINVAL
+    assert "LD_STATIC_SCRATCH_BYTES" in str(e.value)
+    # a colouring with an out-of-range entry is not even read when the grid is too large
+    bad = colour.copy()
+    bad[-1] = -5
+    with pytest.raises(L.LogDetError) as e:
+        L.ld_logdet_static(m, bad, nc, NSHIFT, TOL)
     assert "LD_STATIC_SCRATCH_BYTES" in str(e.value)
