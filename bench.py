@@ -215,7 +215,7 @@ def roofline_entry(kernel, n, T, word, r, keep_x, bq_per_pass, peak, src, traffi
             "pass_words": info["pass_words"], "peak_source": src}
 
 
-def config_posterior2048(L, steps, peak, src):
+def config_posterior2048(L, steps, peak, src, warmup=1, fp64=True):
     """configs[3]: Gauss-linear posterior Q_p = 0.1 I - Lap + 4 diag(mask) on 2048 x 2048
     (10 % observed, seeded), distance 4, N = 20, log det and gradient (kappa^2, tau) per
     evaluation; mixed precision with reliable updates (tol 1e-9) against the plain FP64
@@ -225,22 +225,32 @@ def config_posterior2048(L, steps, peak, src):
     mask = synth.obs_mask(4, n, 0.1)
     out = {}
     for name, prec, delta in (("mixed", L.LD_MIXED, 1e-2), ("fp64", L.LD_FP64, 0.0)):
+        if name == "fp64" and not fp64:
+            continue
         ctx = L.ld_create(L.grid_matrix(L.LD_STENCIL_2D5, dims, k2, tau=tau, obs_mask=mask), 4, 20, 1e-9,
                           L.options(precision=prec, reliable_delta=delta))
-        timed_evals(L, ctx, 1, grad=[L.LD_P_KAPPA2, L.LD_P_TAU])
+        if warmup:
+            timed_evals(L, ctx, warmup, grad=[L.LD_P_KAPPA2, L.LD_P_TAU])
         out[name] = timed_evals(L, ctx, steps if name == "mixed" else 1, grad=[L.LD_P_KAPPA2, L.LD_P_TAU])
         del ctx
-    m, f = out["mixed"], out["fp64"]
+    m = out["mixed"]
     info = m["info"]
     T = info["tile_width"]
-    roof = roofline_entry("k_lean2d (5-point, seed solution kept)", n, T, 4, m, True, n, peak, src)
-    return {"workload": "2048x2048 posterior, kappa^2 0.1, tau 4, 10% mask, d=4, N=20, tol 1e-9, grad (kappa^2, tau)",
-            "value": steps / (m["ms"] / 1e3), "unit": UNIT, "evaluations": steps,
-            "dtype": "f32 vectors / f64 scalars, reliable updates", "roofline": roof,
-            "n_colours": info["n_colours"], "iters": info["iters"], "reliable_updates": info["reliable_updates"],
-            "rel_resid_max": info["rel_resid_max"],
-            "fp64_form": {"value": 1.0 / (f["ms"] / 1e3), "logdet_rel_diff": abs(m["logdet"] - f["logdet"]) / abs(f["logdet"]),
-                          "grad_rel_diff": [abs(a - b) / abs(b) for a, b in zip(m["grad"], f["grad"])]}}
+    lean = info["pass_words"] == 6
+    roof = roofline_entry("k_lean2d (5-point, seed solution kept)" if lean else "k_stream2d (5-point, stored w)",
+                          n, T, 4, m, True, n, peak, src,
+                          traffic=recorded_traffic("k_lean2d_posterior2048_T2.md") if lean and T == 2 else None)
+    res = {"workload": "2048x2048 posterior, kappa^2 0.1, tau 4, 10% mask, d=4, N=20, tol 1e-9, grad (kappa^2, tau)",
+           "value": steps / (m["ms"] / 1e3), "unit": UNIT, "evaluations": steps,
+           "dtype": "f32 vectors / f64 scalars, reliable updates", "roofline": roof,
+           "n_colours": info["n_colours"], "iters": info["iters"], "reliable_updates": info["reliable_updates"],
+           "rel_resid_max": info["rel_resid_max"]}
+    if fp64:
+        f = out["fp64"]
+        res["fp64_form"] = {"value": 1.0 / (f["ms"] / 1e3),
+                            "logdet_rel_diff": abs(m["logdet"] - f["logdet"]) / abs(f["logdet"]),
+                            "grad_rel_diff": [abs(a - b) / abs(b) for a, b in zip(m["grad"], f["grad"])]}
+    return res
 
 
 def config_periodic64(L, steps):
@@ -359,6 +369,22 @@ def run_small_configs(args):
                 "config": {"workload": r.pop("workload")}}
         line.update(r)
         print(json.dumps(line), flush=True)
+
+
+def run_posterior(args):
+    """configs[3] alone (the 2048^2 posterior, mixed with reliable updates, gradient), one
+    JSON line; `--steps 1 --warmup 0 --fp64-sample 0` runs a single evaluation."""
+    import torch
+    import paper_1105_5256_gb300 as L
+    torch.cuda.set_device(0)
+    L.library(build_if_missing=True)
+    peak, src = peak_hbm()
+    r = config_posterior2048(L, max(args.steps, 1), peak, src, warmup=args.warmup, fp64=args.fp64_sample > 0)
+    line = {"metric": "log-det+grad evals/sec (2048^2 Gauss-linear posterior, d=4, N=20)", "value": r.pop("value"),
+            "unit": UNIT, "n_gpus": 1, "steps": r["evaluations"], "warmup": args.warmup, "higher_is_better": True,
+            "dtype": r.pop("dtype"), "data": "synthetic", "config": {"workload": r.pop("workload")}}
+    line.update(r)
+    print(json.dumps(line), flush=True)
 
 
 def run_field3d(args):
@@ -682,7 +708,7 @@ def main():
     ap.add_argument("--split", default="batches", choices=["batches", "colours"],
                     help="several GPUs: independent batches per rank, or every evaluation's colours split")
     ap.add_argument("--workload", default="matern1024",
-                    choices=["matern1024", "batch256", "field3d256", "small"])
+                    choices=["matern1024", "batch256", "field3d256", "small", "posterior2048"])
     ap.add_argument("--side", type=int, default=256, help="field3d256 workload: grid side")
     ap.add_argument("--fp64-sample", type=int, default=2,
                     help="draws also evaluated in the plain FP64 form (mixed precision runs)")
@@ -697,6 +723,8 @@ def main():
         run_field3d(args)
     elif args.workload == "small":
         run_small_configs(args)
+    elif args.workload == "posterior2048":
+        run_posterior(args)
     else:
         run_ours(args)
 
