@@ -1609,27 +1609,11 @@ ld_status ld_grid_bounds(const ld_matrix *Q, double *lmin, double *lmax) {
     return LD_OK;
 }
 
-ld_status ld_batch_create(int count, const ld_matrix *Qs, const int *distances, int n_shifts,
-                          double tol, const ld_options *opt_in, ld_ctx **out) {
-    if (!out) return fail(LD_EINVAL, "out is NULL");
-    *out = nullptr;
-    if (count < 1 || !Qs || !distances) return fail(LD_EINVAL, "count >= 1 with Qs and distances");
-    ld_options opt;
-    ld_default_options(&opt);
-    if (opt_in) opt = *opt_in;
-    if (opt.precision != LD_FP64 && opt.precision != LD_MIXED) return fail(LD_EINVAL, "bad precision");
-    if (n_shifts < 1 || n_shifts > 256) return fail(LD_EINVAL, "n_shifts must be in [1, 256]");
-    if (!(tol > 0.0 && tol < 1.0)) return fail(LD_EINVAL, "tol must be in (0, 1)");
-    if (opt.max_iter < 0) return fail(LD_EINVAL, "max_iter must be >= 0");
-    // every instance is checked on the host before any device work
-    for (int i = 0; i < count; ++i) {
-        if (ld_status v = validate_matrix(&Qs[i])) {
-            std::string msg = g_err;
-            return fail(v, "instance %d: %s", i, msg.c_str());
-        }
-        if (Qs[i].kind == LD_CSR) return fail(LD_EUNSUPPORTED, "batched instances are grid kinds");
-        if (distances[i] < 0) return fail(LD_EINVAL, "instance %d: colouring_distance must be >= 0", i);
-    }
+// Build a batch context with tile width T.  step_s: seconds of one CTA step (one lattice
+// row of 128 vertices) of the persistent engine, from the tuner's measurement; an instance
+// whose one-CTA solve would outlast the batch runs on the grid engine (step_s <= 0: none).
+ld_status batch_build(int count, const ld_matrix *Qs, const int *distances, int n_shifts, double tol,
+                      const ld_options &opt, int T, double step_s, ld_ctx **out) {
     ld_ctx *c = new (std::nothrow) ld_ctx();
     if (!c) return fail(LD_ENOMEM, "host allocation");
     std::unique_ptr<ld_ctx> guard(c);
@@ -1648,21 +1632,21 @@ ld_status ld_batch_create(int count, const ld_matrix *Qs, const int *distances, 
     // Every instance gets a context with a common tile width.  A tile in the persistent
     // launch is one CTA's whole solve, so an instance whose solve would outlast the rest
     // of the batch (CG iterations ~ 8 sqrt(cond), a lattice row of 128 vertices per CTA
-    // step of about a microsecond: more than 0.8 s) runs on the multi-CTA grid engine
-    // instead, on its own stream beside the persistent launch.
+    // step of step_s: more than 0.8 s) runs on the multi-CTA grid engine instead, on its
+    // own stream beside the persistent launch.
     ld_options sub = opt;
     sub.keep_x0 = 0;
     sub.colouring = nullptr;
-    if (sub.tile_width == 0) sub.tile_width = opt.precision == LD_MIXED ? 2 : 1;
-    c->T = sub.tile_width;
+    sub.tile_width = T;
+    c->T = T;
     c->subs.reserve(count);
     for (int i = 0; i < count; ++i) {
         if (Qs[i].kind == LD_CSR) return fail(LD_EUNSUPPORTED, "batched instances are grid kinds");
         double lo = 0.0, hi = 0.0;
         if (ld_status st = ld_grid_bounds(&Qs[i], &lo, &hi)) return st;
         int32_t dd[3] = {Qs[i].dims[0], Qs[i].dims[1], Qs[i].kind == LD_STENCIL_3D7 ? Qs[i].dims[2] : 1};
-        const double est_s = 8.0 * std::sqrt(hi / lo) * ((double)grid_n(dd) / 128.0) * 1.2e-6;
-        const bool large = est_s > 0.8 && grid_n(dd) >= 32768;
+        const double est_s = 8.0 * std::sqrt(hi / lo) * ((double)grid_n(dd) / 128.0) * step_s;
+        const bool large = step_s > 0.0 && est_s > 0.8 && grid_n(dd) >= 32768;
         ld_options o = sub;
         o.engine = large ? 1 : 2;
         o.cuda_stream = large ? nullptr : c->stream;
@@ -1730,6 +1714,96 @@ ld_status ld_batch_create(int count, const ld_matrix *Qs, const int *distances, 
     }
     *out = guard.release();
     return LD_OK;
+}
+
+
+// Tile width and step cost of a batch, tuned once per batch shape and process: for every
+// candidate tile width the persistent launch runs 16 iterations of every instance (all in
+// the persistent engine); the fastest width wins, and its time gives the cost of one CTA
+// step (total lattice-row steps over the resident CTAs) for the engine split.
+std::map<std::string, std::pair<int, double>> g_batch_tune;
+
+std::string batch_key(int count, const ld_matrix *Qs, const int *distances, int n_shifts, int precision) {
+    std::ostringstream k;
+    k << "batch:" << precision << ":" << n_shifts << ":" << count;
+    uint64_t h = 1469598103934665603ull;
+    for (int i = 0; i < count; ++i) {
+        const int64_t v[5] = {Qs[i].kind, Qs[i].dims[0], Qs[i].dims[1], Qs[i].kind == LD_STENCIL_3D7 ? Qs[i].dims[2] : 1,
+                              distances[i]};
+        for (int64_t x : v) h = (h ^ (uint64_t)x) * 1099511628211ull;
+    }
+    k << ":" << std::hex << h;
+    return k.str();
+}
+
+ld_status ld_batch_create(int count, const ld_matrix *Qs, const int *distances, int n_shifts,
+                          double tol, const ld_options *opt_in, ld_ctx **out) {
+    if (!out) return fail(LD_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !Qs || !distances) return fail(LD_EINVAL, "count >= 1 with Qs and distances");
+    ld_options opt;
+    ld_default_options(&opt);
+    if (opt_in) opt = *opt_in;
+    if (opt.precision != LD_FP64 && opt.precision != LD_MIXED) return fail(LD_EINVAL, "bad precision");
+    if (n_shifts < 1 || n_shifts > 256) return fail(LD_EINVAL, "n_shifts must be in [1, 256]");
+    if (!(tol > 0.0 && tol < 1.0)) return fail(LD_EINVAL, "tol must be in (0, 1)");
+    if (opt.max_iter < 0) return fail(LD_EINVAL, "max_iter must be >= 0");
+    if (opt.tile_width != 0 && choose_tile(opt.precision, 1, opt.tile_width) < 0)
+        return fail(LD_EINVAL, "tile_width %d not available for this precision", opt.tile_width);
+    // every instance is checked on the host before any device work
+    for (int i = 0; i < count; ++i) {
+        if (ld_status v = validate_matrix(&Qs[i])) {
+            std::string msg = g_err;
+            return fail(v, "instance %d: %s", i, msg.c_str());
+        }
+        if (Qs[i].kind == LD_CSR) return fail(LD_EUNSUPPORTED, "batched instances are grid kinds");
+        if (distances[i] < 0) return fail(LD_EINVAL, "instance %d: colouring_distance must be >= 0", i);
+    }
+    const double default_step = 1.2e-6;   // one CTA step before any measurement
+    int T = opt.tile_width;
+    double step_s = default_step;
+    const std::string key = batch_key(count, Qs, distances, n_shifts, opt.precision);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_batch_tune.find(key);
+        if (it != g_batch_tune.end()) {
+            if (T == 0) T = it->second.first;
+            step_s = it->second.second;
+        }
+    }
+    if (T == 0) {
+        static const int f64[2] = {1, 2}, f32[2] = {2, 4};
+        const int *cand = opt.precision == LD_FP64 ? f64 : f32;
+        double best_ms = 1e300;
+        double steps_per_cta = 0.0;
+        for (int k = 0; k < 2; ++k) {
+            ld_options o = opt;
+            o.max_iter = 16;
+            ld_ctx *t = nullptr;
+            if (batch_build(count, Qs, distances, n_shifts, tol, o, cand[k], 0.0, &t) != LD_OK) continue;
+            std::vector<double> v(count);
+            ld_info info{};
+            ld_batch_logdet(t, v.data(), nullptr, &info);      // warm (usually LD_ENOTCONV)
+            ld_batch_logdet(t, v.data(), nullptr, &info);
+            // lattice-row steps of the trial (16 iterations of every tile) per resident CTA
+            double rows = 0.0;
+            for (ld_ctx *sc : t->subs) rows += 16.0 * sc->ntiles * ((double)sc->n / 128.0);
+            const double per_cta = rows / std::max(1, t->bgrid);
+            ld_destroy(t);
+            if (!(info.ms > 0.0)) continue;
+            if (info.ms < best_ms) {
+                best_ms = info.ms;
+                T = cand[k];
+                steps_per_cta = per_cta;
+            }
+        }
+        g_err = "no error";
+        if (T == 0) T = opt.precision == LD_MIXED ? 2 : 1;
+        else if (steps_per_cta > 0.0) step_s = best_ms * 1e-3 / steps_per_cta;
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_batch_tune[key] = {T, step_s};
+    }
+    return batch_build(count, Qs, distances, n_shifts, tol, opt, T, step_s, out);
 }
 
 ld_status ld_batch_logdet(ld_ctx *c, double *logdets, double *grads, ld_info *info) {

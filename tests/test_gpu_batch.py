@@ -48,7 +48,8 @@ def test_small_batch_matches_single_contexts_and_oracle(prec, tol, rel):
     mats, dists = make(insts)
     b = L.ld_batch_create(mats, dists, NSHIFT, tol, L.options(precision=prec))
     vals, grads, info = L.ld_batch_logdet(b, with_grad=True)
-    T = 2 if prec == L.LD_MIXED else 1
+    T = info["tile_width"]                 # chosen by the batch tuner from the candidates
+    assert T in ((2, 4) if prec == L.LD_MIXED else (1, 2))
     for k, inst in enumerate(insts):
         ctx = L.ld_create(L.grid_matrix(inst.kind, inst.dims, inst.kappa2), inst.distance, NSHIFT,
                           tol, L.options(precision=prec, engine=2, tile_width=T))
@@ -66,6 +67,24 @@ def test_small_batch_matches_single_contexts_and_oracle(prec, tol, rel):
             assert abs(grads[k] - gref) <= 1e-5 * abs(gref)
         else:
             assert np.isnan(grads[k])
+
+
+def test_batch_tile_width_explicit_and_tuned_agree():
+    """The tuner's choice and every explicit candidate width give the same log dets (the
+    columns' recurrences do not depend on how they are grouped into tiles), and a width
+    the precision does not offer is rejected before any device work."""
+    insts = synth.batch_instances(9, count=8, side_lo=24, side_hi=64)
+    mats, dists = make(insts)
+    tol = 1e-9
+    tuned, _, info = L.ld_batch_logdet(L.ld_batch_create(mats, dists, NSHIFT, tol, L.options(precision=L.LD_FP64)))
+    for T in (1, 2):
+        vals, _, i2 = L.ld_batch_logdet(L.ld_batch_create(mats, dists, NSHIFT, tol,
+                                                          L.options(precision=L.LD_FP64, tile_width=T)))
+        assert i2["tile_width"] == T
+        assert np.max(np.abs(vals - tuned) / np.abs(tuned)) <= 1e-9
+    with pytest.raises(L.LogDetError) as e:
+        L.ld_batch_create(mats, dists, NSHIFT, tol, L.options(precision=L.LD_MIXED, tile_width=3))
+    assert e.value.status == L.LD_EINVAL
 
 
 def test_batch_reuse_is_deterministic():
