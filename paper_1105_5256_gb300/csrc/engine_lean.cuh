@@ -44,7 +44,7 @@
 
 namespace ld {
 
-constexpr int LEAN_NT = 128;      // threads per CTA
+constexpr int LEAN_NT = 96;       // threads per CTA (3 warps: strips of 192 columns at X = 2)
 constexpr int LEAN_PD = 8;        // ring depth (rows; a power of two)
 constexpr uint8_t LEAN_NONE = 0xFF;
 
