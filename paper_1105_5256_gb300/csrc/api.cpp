@@ -1045,6 +1045,8 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
     s.result = s.terms + 2 * C;
     s.lean = 0;
     s.lane = nullptr;
+    // the lean 5-point pass forms kappa^2 + tau mask_i from a mask bit in its lane codes
+    s.lane_mask = (c->kind == LD_STENCIL_2D5 && c->has_mask && !c->has_field) ? 1 : 0;
     int bpt_max = 0;
     for (int kx = 0; kx < 2; ++kx) {   // the lean lattice pass plans its own strips
         Solve t = s;

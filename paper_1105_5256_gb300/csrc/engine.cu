@@ -730,11 +730,12 @@ size_t engine_lean_code_bytes(const Solve &s) {
     return (size_t)s.ntiles * s.strips * s.op.ny * swl;
 }
 
-// Lane codes of the lean pass in strip layout, [tile][strip][row][SWL]: colour - tile*T
-// when that is a column of the tile and the vertex is owned by the strip, else LEAN_NONE
-// (halo and out-of-grid columns)
-__global__ void k_lean_codes(const int32_t *colour, int nx, int ny, int T, int ntiles, int strips,
-                             int SWL, int XH, int W, uint8_t *out) {
+// Lane codes of the lean pass in strip layout, [tile][strip][row][SWL]: in the low seven
+// bits colour - tile*T when that is a column of the tile and the vertex is owned by the
+// strip, else LEAN_NONE; in the high bit (when the pass takes its diagonal from the codes)
+// the mask bit of the column's vertex, for every in-grid or wrapped column of the strip.
+__global__ void k_lean_codes(const int32_t *colour, const uint8_t *mask, int nx, int ny, int periodic, int T,
+                             int ntiles, int strips, int SWL, int XH, int W, uint8_t *out) {
     const int64_t total = (int64_t)ntiles * strips * ny * SWL;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
          q += (int64_t)gridDim.x * blockDim.x) {
@@ -750,6 +751,11 @@ __global__ void k_lean_codes(const int32_t *colour, int nx, int ny, int T, int n
             const int lc = colour[(int64_t)y * nx + gx] - tile * T;
             if (lc >= 0 && lc < T) c = (uint8_t)lc;
         }
+        if (mask) {
+            int g = gx;
+            if (periodic) g = ((g % nx) + nx) % nx;
+            if (g >= 0 && g < nx && mask[(int64_t)y * nx + g]) c |= LEAN_MASK_BIT;
+        }
         out[q] = c;
     }
 }
@@ -761,7 +767,8 @@ int engine_lean_codes(const Solve &s, uint8_t *out, void *stream) {
     int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
     if (blocks < 1) blocks = 1;
     k_lean_codes<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        s.colour, s.op.nx, s.op.ny, s.T, s.ntiles, s.strips, swl, xh, w, out);
+        s.colour, s.lane_mask ? s.op.mask : nullptr, s.op.nx, s.op.ny, s.op.periodic, s.T, s.ntiles, s.strips,
+        swl, xh, w, out);
     return (int)cudaGetLastError();
 }
 

@@ -38,7 +38,10 @@
 // barrier per row for all levels.  Outputs of rows or columns outside a Dirichlet grid
 // are zero (the ghost values of the difference form; copies of such rows zero-fill); a
 // torus wraps.  The colour of a vertex enters only through a per-tile lane code (one
-// byte: its column in the tile, or LEAN_NONE), read for the rows whose dots are taken.
+// byte: its column in the tile in the low seven bits, or LEAN_NONE), read for the rows whose
+// dots are taken; for the 5-point kind with a scalar kappa^2 and an observation mask the
+// code's high bit carries the vertex's mask bit, and the diagonal kappa^2 + tau mask_i is
+// formed from it instead of read as a word.
 #pragma once
 #include "engine_device.cuh"
 
@@ -46,7 +49,8 @@ namespace ld {
 
 constexpr int LEAN_NT = 96;       // threads per CTA (3 warps: strips of 192 columns at X = 2)
 constexpr int LEAN_PD = 8;        // ring depth (rows; a power of two)
-constexpr uint8_t LEAN_NONE = 0xFF;
+constexpr uint8_t LEAN_NONE = 0x7F;      // lane code of a vertex outside the tile's columns
+constexpr uint8_t LEAN_MASK_BIT = 0x80;  // high bit of a lane code: the vertex is observed
 
 template <int KIND>
 struct LeanGeom {
@@ -202,7 +206,7 @@ __device__ __forceinline__ void lean_dots(LeanAcc<T> &acc, const LRow<T, X> &rk,
     constexpr int H = T / 2;
 #pragma unroll
     for (int j = 0; j < X; ++j) {
-        const int lc = codes[j];
+        const int lc = codes[j] & 0x7F;
 #pragma unroll
         for (int q = 0; q < H; ++q) {
             const int k = j * H + q;
@@ -286,7 +290,11 @@ __device__ __forceinline__ void lean_sweep(const Solve &s, int tile, int cur, in
     float *const rn = static_cast<float *>(cur ? s.rbuf[0] : s.rbuf[1]) + off;
     float *const sn = static_cast<float *>(cur ? s.pbuf[0] : s.pbuf[1]) + off;
     float *const xs = KEEPX ? static_cast<float *>(s.x) + off : nullptr;
-    const float *const diag = MAT ? nullptr : s.op.diag_f;
+    // 5-point diagonal: from the codes' mask bit (scalar kappa^2 with a mask), the FP32 word
+    // array (kappa^2 field), or the scalar kappa^2
+    const bool mbit = !MAT && s.lane_mask;
+    const float *const diag = MAT || mbit ? nullptr : s.op.diag_f;
+    const float tauf = s.op.tau_f;
     const uint8_t *const code = s.lane + ((int64_t)tile * s.strips + strip) * (int64_t)ny * SWL;
     const int cb = tile * T;
     // per-column coefficients: -alpha s (level-1 update), beta, alpha (seed solution)
@@ -330,8 +338,8 @@ __device__ __forceinline__ void lean_sweep(const Solve &s, int tile, int cur, in
             }
         }
         if (tid < SWL / 16) {
-            const bool cin = lrow >= ys && lrow < ye;
-            lean_cp<16>(base + S::o_c + tid * 16, code + (int64_t)(cin ? lrow : 0) * SWL + tid * 16, cin);
+            const bool cin = lrow < yend && (per || (unsigned)lrow < (unsigned)ny);
+            lean_cp<16>(base + S::o_c + tid * 16, code + (int64_t)(cin ? lwr : 0) * SWL + tid * 16, cin);
         }
         asm volatile("cp.async.commit_group;\n" ::);
         ++lrow;
@@ -410,8 +418,13 @@ __device__ __forceinline__ void lean_sweep(const Solve &s, int tile, int cur, in
                 float d1[X], d2[X];
 #pragma unroll
                 for (int j = 0; j < X; ++j) {
-                    d1[j] = diag ? reinterpret_cast<const float *>(s1 + S::o_d)[xl0 + j] : k2;
-                    d2[j] = diag ? reinterpret_cast<const float *>(s2 + S::o_d)[xl0 + j] : k2;
+                    if (mbit) {
+                        d1[j] = k2 + ((s1 + S::o_c)[xl0 + j] & LEAN_MASK_BIT ? tauf : 0.f);
+                        d2[j] = k2 + ((s2 + S::o_c)[xl0 + j] & LEAN_MASK_BIT ? tauf : 0.f);
+                    } else {
+                        d1[j] = diag ? reinterpret_cast<const float *>(s1 + S::o_d)[xl0 + j] : k2;
+                        d2[j] = diag ? reinterpret_cast<const float *>(s2 + S::o_d)[xl0 + j] : k2;
+                    }
                 }
                 const Row q = lean_level<T, X>(d1, U[P2], U[P1], U[PH], lf, rt);
                 Row rk, pk;

@@ -77,6 +77,8 @@ struct Solve {
                            // lean pass (state r and p, or r and u = Q1 p for the Matern
                            // kind; w recomputed), X lattice columns per thread
     const uint8_t *lane;   // lean pass: per-tile lane codes in strip layout (or null)
+    int lane_mask;         // lean pass, 5-point, scalar kappa^2 with a mask: the codes' high
+                           // bit is the mask bit (diagonal kappa^2 + tau mask_i formed in the pass)
     int tile0, tstride;    // grid engine: a launch covers tiles tile0, tile0 + tstride, ...
                            // (grid.y of them; tstride 0 reads as 1)
     int precision;         // 0 fp64, 1 mixed

@@ -118,3 +118,38 @@ def test_lean_pass_repeated_solves_are_deterministic():
     v2, i2 = L.ld_logdet(ctx)
     assert i1["pass_words"] == 4 and i2["pass_words"] == 4
     assert v1 == v2
+
+
+@pytest.mark.parametrize("dims,per", [((260, 130), False), ((120, 90), True), ((97, 64), False)])
+def test_lean_pass_masked_posterior_diagonal_from_codes(dims, per):
+    """Gauss-linear posterior Q = kappa^2 I - Lap + tau diag(mask) (Sec. 1): the lean pass
+    forms kappa^2 + tau mask_i from the mask bit of its lane codes (halo and wrapped columns
+    included); terms against the exact sparse-LU rational target and against the stored-w
+    pass, which reads the diagonal as a word, with the gradients (kappa^2, tau)."""
+    import synth
+    from oracle import probing
+    import scipy.sparse.linalg as spla
+    n = dims[0] * dims[1]
+    k2, tau = 0.1, 4.0
+    mask = synth.obs_mask(11, n, 0.1)
+    Q = om.precision(om.KIND_2D5, dims, k2, periodic=per, tau=tau, mask=mask)
+    out = {}
+    for lp in (0, 1):
+        ctx = L.ld_create(L.grid_matrix(om.KIND_2D5, dims, k2, periodic=per, tau=tau, obs_mask=mask), 4, 20,
+                          1e-7, L.options(precision=L.LD_MIXED, engine=1, tile_width=2, lattice_pass=lp))
+        v, g, info = L.ld_logdet_grad(ctx, [L.LD_P_KAPPA2, L.LD_P_TAU])
+        out[lp] = (v, g, info, L.ld_column_terms(ctx)[0])
+        col, _ = checked_colouring(ctx, Q, 4)
+    assert out[0][2]["pass_words"] == 6 and out[1][2]["pass_words"] == 8
+    lo, hi = mt.spectral_bounds(om.KIND_2D5, dims, k2, periodic=per, tau=tau, mask=mask)
+    s, a = hht.log_nodes(lo, hi, 20)
+    ref = mt.probed_rational_splu(Q, col, s, a, per_colour=True)
+    V = probing.probing_vectors(col)
+    X = spla.splu(Q.tocsc()).solve(V)
+    gref = [float(np.sum(V * X)), float(np.sum((mask[:, None] * V) * X))]
+    for lp in (0, 1):
+        v, g, info, terms = out[lp]
+        assert np.abs(terms - ref).max() <= 2e-5 * np.abs(ref).max()
+        for got, r in zip(g, gref):
+            assert abs(got - r) <= 2e-5 * abs(r)
+    assert np.abs(out[0][3] - out[1][3]).max() <= 2e-5 * np.abs(ref).max()
