@@ -144,11 +144,11 @@ def moved_bytes(n, T, word, tile_iters, pass_words, lean):
     return (pass_words * T * word + (1 if lean else 4)) * n * tile_iters
 
 
-def pass_kernel_sha256():
-    """sha256 over the sources of the pass kernels (device code and their launcher)."""
+def pass_kernel_sha256(names=("engine_device.cuh", "engine_lean.cuh")):
+    """sha256 over the device sources of a pass kernel (the lean lattice pass by default)."""
     import hashlib
     h = hashlib.sha256()
-    for name in ("engine_device.cuh", "engine_lean.cuh", "engine_iter.cuh"):
+    for name in names:
         h.update(open(os.path.join(ROOT, "paper_1105_5256_gb300", "csrc", name), "rb").read())
     return h.hexdigest()
 
@@ -160,8 +160,9 @@ def recorded_traffic(profile):
     path = os.path.join(ROOT, "profiles", profile)
     try:
         rec = dict(line.split(": ", 1) for line in open(path).read().splitlines()
-                   if line.startswith(("engine_sha256: ", "traffic_bytes_per_pass: ")))
-        if rec.get("engine_sha256", "").strip() != pass_kernel_sha256():
+                   if line.startswith(("engine_sha256: ", "engine_sources: ", "traffic_bytes_per_pass: ")))
+        names = tuple(rec.get("engine_sources", "engine_device.cuh engine_lean.cuh").split())
+        if rec.get("engine_sha256", "").strip() != pass_kernel_sha256(names):
             return None
         return float(rec["traffic_bytes_per_pass"])
     except (OSError, KeyError, ValueError):
@@ -299,6 +300,96 @@ def config_field3d(L, side, steps, peak, src, fp64=True):
                             "logdet_rel_diff": abs(r["logdet"] - f["logdet"]) / abs(f["logdet"]),
                             "grad_rel_diff": abs(float(r["grad"][0]) - float(f["grad"][0])) / abs(float(f["grad"][0]))}
     return out
+
+
+def mesh_problem(side, k2h2=0.1, alpha=2):
+    """Seeded perturbed side x side-vertex triangulation of the unit square with its P1 FEM
+    SPDE precision (Sec. 3's SPDE model on a general mesh): kappa^2 = k2h2 / h^2 so that
+    kappa^2 h^2 matches a lattice kappa^2 of k2h2.  The spectral interval is a bound from
+    the lumped mass c (one third of each incident triangle's area): lambda_min >=
+    kappa^4 min(c)^2 / max(c) for alpha = 2 (kappa^2 min(c) for alpha = 1), lambda_max <=
+    the largest absolute row sum."""
+    from paper_1105_5256_gb300 import mesh
+    p, t = synth.perturbed_triangulation(6, side, side)
+    h = 1.0 / (side - 1)
+    k2 = k2h2 / h ** 2
+    rp, ci, vv = mesh.spde_csr(p, t, k2, alpha, 1.0)
+    e1, e2 = p[t[:, 1]] - p[t[:, 0]], p[t[:, 2]] - p[t[:, 0]]
+    area = 0.5 * np.abs(e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0])
+    c = np.bincount(t.ravel(), weights=np.repeat(area / 3.0, 3), minlength=p.shape[0])
+    lo = k2 * k2 * c.min() ** 2 / c.max() if alpha == 2 else k2 * c.min()
+    hi = float(np.add.reduceat(np.abs(vv), rp[:-1]).max())
+    return rp, ci, vv, lo, hi
+
+
+def config_mesh(L, side, steps, peak, src, matfree=True, fp64=True, T=0):
+    """General-mesh input: the alpha = 2 FEM SPDE precision on a perturbed side x side-vertex
+    triangulation as a CSR matrix, distance 2 in G(Q), N = 20, tol 1e-6; mixed precision on
+    the fused CSR pass, beside the plain FP64 form and the matrix-free path with a cuSPARSE
+    CSR product (torch) as the caller's callback, both FP64."""
+    import torch
+    rp, ci, vv, lo, hi = mesh_problem(side)
+    n, nnz = rp.size - 1, ci.size
+    out = {}
+    for name, prec in (("mixed", L.LD_MIXED), ("fp64", L.LD_FP64)):
+        if name == "fp64" and not (fp64 or matfree):
+            continue
+        ctx = L.ld_create(L.csr_matrix(rp, ci, vv), 2, 20, 1e-6,
+                          L.options(precision=prec, lambda_min=lo, lambda_max=hi,
+                                    tile_width=T if name == "mixed" else 0))
+        timed_evals(L, ctx, 1)
+        out[name] = timed_evals(L, ctx, steps if name == "mixed" else 1)
+        col, nc = L.ld_get_colouring(ctx)
+        del ctx
+    m, f = out["mixed"], out.get("fp64")
+    info = m["info"]
+    T = info["tile_width"]
+    # the matrix once per pass: nnz (4-byte index + 4-byte value) + the 8-byte row pointer
+    roof = roofline_entry("k_csr_step + k_csr_spmv (CSR)", n, T, 4, m, False, nnz * 8 + 8 * n, peak, src)
+    res = {"workload": "perturbed %dx%d-vertex triangulation, P1 FEM SPDE alpha=2, kappa^2 h^2 0.1, "
+                       "d=2, N=20, tol 1e-6" % (side, side),
+           "value": steps / (m["ms"] / 1e3), "unit": UNIT, "evaluations": steps,
+           "dtype": "f32 vectors / f64 scalars", "n": n, "nnz": nnz, "n_colours": info["n_colours"],
+           "tile_width": T, "iters": info["iters"], "engine": info["engine"], "roofline": roof,
+           "lambda_bounds": [lo, hi]}
+    if f is not None:
+        res["fp64_form"] = {"value": 1.0 / (f["ms"] / 1e3), "iters": f["info"]["iters"],
+                            "logdet_rel_diff": abs(m["logdet"] - f["logdet"]) / abs(f["logdet"])}
+    if matfree:
+        Qt = torch.sparse_csr_tensor(torch.from_numpy(rp), torch.from_numpy(ci.astype(np.int64)),
+                                     torch.from_numpy(vv), size=(n, n), dtype=torch.float64, device="cuda")
+
+        def mv(P, W):
+            W.copy_(torch.sparse.mm(Qt, P))
+        mf = L.ld_create_matfree(n, mv, col, lo, hi, 20, 1e-6)
+        timed_evals(L, mf, 1)
+        r = timed_evals(L, mf, 1)
+        mi = r["info"]
+        res["matfree_fp64"] = {"value": 1.0 / (r["ms"] / 1e3), "iters": mi["iters"],
+                               "launches_per_iter": mi["gpu_launches"] / max(mi["iters"], 1),
+                               "ms_per_iter": r["ms"] / max(mi["iters"], 1),
+                               "logdet_rel_diff": abs(r["logdet"] - f["logdet"]) / abs(f["logdet"]) if f else None,
+                               "callback": "torch.sparse.mm on a CSR tensor (cuSPARSE SpMM) + copy"}
+        del mf
+    return res
+
+
+def run_mesh(args):
+    """The general-mesh workload alone (--side vertices a side, 1024 by default), one line."""
+    import torch
+    import paper_1105_5256_gb300 as L
+    torch.cuda.set_device(0)
+    L.library(build_if_missing=True)
+    peak, src = peak_hbm()
+    side = args.side if args.side != 256 else 1024
+    r = config_mesh(L, side, max(args.steps, 1), peak, src, matfree=args.fp64_sample > 0,
+                    fp64=args.fp64_sample > 0, T=args.tile_width)
+    line = {"metric": "log-det evals/sec (FEM SPDE alpha=2 on a %d^2-vertex mesh, CSR, d=2, N=20)" % side,
+            "value": r.pop("value"), "unit": UNIT, "n_gpus": 1, "steps": r["evaluations"], "warmup": 1,
+            "higher_is_better": True, "dtype": r.pop("dtype"), "data": "synthetic (seeded mesh)",
+            "config": {"workload": r.pop("workload")}}
+    line.update(r)
+    print(json.dumps(line), flush=True)
 
 
 def run_batch(args):
@@ -532,7 +623,8 @@ def run_ours(args):
         oc = {}
         for key, fn in (("periodic64_csr_fp64", lambda: config_periodic64(L, 10)),
                         ("posterior2048_mixed_grad", lambda: config_posterior2048(L, 3, peak, src)),
-                        ("field3d256_mixed_grad", lambda: config_field3d(L, 256, 1, peak, src))):
+                        ("field3d256_mixed_grad", lambda: config_field3d(L, 256, 1, peak, src)),
+                        ("mesh1024_csr_mixed", lambda: config_mesh(L, 1024, 2, peak, src))):
             try:
                 oc[key] = fn()
             except Exception as e:      # a failing side configuration must not lose the headline
@@ -708,8 +800,9 @@ def main():
     ap.add_argument("--split", default="batches", choices=["batches", "colours"],
                     help="several GPUs: independent batches per rank, or every evaluation's colours split")
     ap.add_argument("--workload", default="matern1024",
-                    choices=["matern1024", "batch256", "field3d256", "small", "posterior2048"])
-    ap.add_argument("--side", type=int, default=256, help="field3d256 workload: grid side")
+                    choices=["matern1024", "batch256", "field3d256", "small", "posterior2048", "mesh1024"])
+    ap.add_argument("--side", type=int, default=256,
+                    help="grid side (field3d256 workload) or mesh vertices a side (mesh1024, 256 = 1024)")
     ap.add_argument("--fp64-sample", type=int, default=2,
                     help="draws also evaluated in the plain FP64 form (mixed precision runs)")
     ap.add_argument("--kappa2", type=float, default=0.0,
@@ -725,6 +818,8 @@ def main():
         run_small_configs(args)
     elif args.workload == "posterior2048":
         run_posterior(args)
+    elif args.workload == "mesh1024":
+        run_mesh(args)
     else:
         run_ours(args)
 

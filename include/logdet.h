@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define LD_ABI_VERSION 5
+#define LD_ABI_VERSION 6
 
 typedef struct ld_ctx ld_ctx;
 
@@ -144,8 +144,9 @@ typedef struct {
                                  one CG pass reads plus writes for the solve state -- 4 for the
                                  lean lattice pass (FP32 on 2D lattices: r and p, or r and Q1 p
                                  for the Matern kind, with Q p recomputed), 6 for the stored-w
-                                 pass (r, Q p, p), plus 2 when the pass also updates the kept
-                                 seed solution; -1 for the other engines */
+                                 pass (r, Q p, p), 8 for the CSR pass (its step, then its
+                                 product re-reads r and p), plus 2 when the pass also updates
+                                 the kept seed solution; -1 for the other engines */
 } ld_info;
 
 /* ABI version (LD_ABI_VERSION).  Never fails. */
@@ -178,11 +179,17 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
  * Enqueue W = Q P on `stream` (a cudaStream_t; or finish the product before returning).
  * P_dev and W_dev are device arrays of n x ncols doubles owned by the library, row-major (entry
  * (i, c) at i * ncols + c; column c is the probing vector of colour colour_begin + c of
- * the solve); P is read-only, every entry of W must be written.  Called once per CG
- * iteration from the thread that called ld_logdet / ld_logdet_partial.  Return 0 on
- * success; anything else stops the solve with LD_ECALLBACK. */
+ * the solve, or right-hand side c of ld_logmv / ld_invsqrt_mv); P is read-only, every
+ * entry of W must be written.  Called once per CG iteration from the thread that called
+ * the solve.  Return 0 on success; anything else stops the solve with LD_ECALLBACK. */
 typedef int (*ld_matvec_fn)(void *user, int64_t n, int32_t ncols, const double *P_dev,
                             double *W_dev, void *stream);
+
+/* Derivative product of a matrix-free operator Q(eta): enqueue Y = (dQ/d eta_param) X on
+ * `stream` for param in [0, n_params) of ld_matfree_set_derivative; layouts, ownership and
+ * the return value as ld_matvec_fn (X_dev read-only, every entry of Y_dev written). */
+typedef int (*ld_dmatvec_fn)(void *user, int32_t param, int64_t n, int32_t ncols,
+                             const double *X_dev, double *Y_dev, void *stream);
 
 /* Create a context for an SPD operator given only by matvec (Sec. 2.1 method without a
  * matrix):
@@ -195,17 +202,30 @@ typedef int (*ld_matvec_fn)(void *user, int64_t n, int32_t ncols, const double *
  *   lambda_min, lambda_max   0 < lambda_min < lambda_max enclosing the spectrum (the
  *                  library cannot estimate them without the matrix).
  *   n_shifts, tol  as ld_create.
- *   opt            NULL = defaults; cuda_stream and max_iter are used, precision must be
- *                  LD_FP64 (LD_EUNSUPPORTED otherwise), the rest is ignored.
- * The solve runs plain CG with the projected multi-shift recurrences in the library's
- * kernels, two reductions per iteration, n x C FP64 vectors r, p, w on the device.  Only
- * ld_logdet, ld_logdet_partial, ld_column_terms (seed projections NaN), ld_get_colouring,
+ *   opt            NULL = defaults; cuda_stream, max_iter and keep_x0 are used, precision
+ *                  must be LD_FP64 (LD_EUNSUPPORTED otherwise), the rest is ignored.
+ * The solve runs CG in its one-reduction form with the projected multi-shift recurrences
+ * in the library's kernels (three launches around each product), n x C FP64 vectors
+ * r, p, w (and x with keep_x0 or a gradient) on the device; the seed system Q x = v_c is
+ * followed to the tolerance like the shifted ones, so ld_column_terms reports its
+ * projections.  ld_logdet, ld_logdet_partial, ld_logdet_grad and ld_grad (after
+ * ld_matfree_set_derivative), ld_column_terms, ld_logmv, ld_invsqrt_mv, ld_get_colouring,
  * ld_get_nodes and ld_destroy accept the context; the rest return LD_EUNSUPPORTED.
  * Errors: LD_EINVAL (checked before any device call), LD_EUNSUPPORTED, LD_ENOMEM,
- * LD_ECUDA; ld_logdet adds LD_ECALLBACK, LD_ENOTSPD, LD_ENOTCONV, LD_ENUMERIC. */
+ * LD_ECUDA; the solves add LD_ECALLBACK, LD_ENOTSPD, LD_ENOTCONV, LD_ENUMERIC. */
 ld_status ld_create_matfree(int64_t n, ld_matvec_fn matvec, void *user, const int32_t *colouring,
                             double lambda_min, double lambda_max, int n_shifts, double tol,
                             const ld_options *opt, ld_ctx **out);
+
+/* Register the derivative products of a matrix-free context (the gradient of Sec. 3's
+ * likelihood, d log det Q / d eta_j = tr(Q^{-1} dQ/d eta_j), probed as
+ * sum_c v_c^T (dQ/d eta_j) Q^{-1} v_c with the seed solutions of the same solve).  After
+ * it, ld_logdet_grad and ld_grad take parameter ids in [0, n_params) instead of LD_P_*.
+ *   dmatvec, user  the callback and its argument (borrowed for the context's lifetime);
+ *                  dmatvec NULL unregisters.
+ *   n_params       1 <= n_params <= 3.
+ * Errors: LD_EINVAL (bad arguments or not a matrix-free context).  Host only. */
+ld_status ld_matfree_set_derivative(ld_ctx *ctx, ld_dmatvec_fn dmatvec, void *user, int n_params);
 
 /* Replace kappa2 (or its field multiplier), tau and scale, keeping the pattern and
  * colouring (Sec. 3: colourings are computed once and stored).  Spectral bounds and
@@ -219,7 +239,8 @@ ld_status ld_logdet(ld_ctx *ctx, double *logdet, ld_info *info);
 
 /* log det Q and grad[i] = d log det Q / d eta_{ids[i]} ~ sum_c (E v_c)^T Q^{-1} v_c,
  * E = dQ/d eta (tr(Q^{-1} dQ/d eta) probed with the same v_c and the CG seed
- * solutions).  ids from LD_P_*; n_params in [1, 3]. */
+ * solutions).  ids from LD_P_* (matrix-free contexts: indices of the parameters of
+ * ld_matfree_set_derivative, LD_EINVAL when none is registered); n_params in [1, 3]. */
 ld_status ld_logdet_grad(ld_ctx *ctx, int n_params, const int *param_ids, double *logdet,
                          double *grad, ld_info *info);
 
@@ -235,8 +256,7 @@ ld_status ld_logdet_partial(ld_ctx *ctx, int colour_begin, int colour_end, doubl
                             ld_info *info);
 
 /* Per-colour terms of the last solve: terms[c] = Re sum_l alpha_l v_c^T x^{sigma_l}_c
- * (n_colours doubles) and, if seed != NULL, seed[c] = v_c^T Q^{-1} v_c (NaN for a
- * matrix-free context, whose seed system is not followed to convergence).
+ * (n_colours doubles) and, if seed != NULL, seed[c] = v_c^T Q^{-1} v_c.
  * LD_EINVAL before the first completed solve. */
 ld_status ld_column_terms(const ld_ctx *ctx, double *terms, double *seed);
 
@@ -256,7 +276,8 @@ ld_status ld_apply(ld_ctx *ctx, int ncols, const double *x, double *y);
  * plus one complex search direction per shift, accumulating y directly.  V, Y host arrays,
  * row-major n x ncols, FP64 (the vectors run in the context's precision).  Uses the
  * context's operator, nodes and tolerance; needs about (6 w + 16 N + 8) n ncols bytes of
- * device memory for the call.  Errors as ld_logdet. */
+ * device memory for the call (a matrix-free context: the caller's product, FP64 vectors,
+ * (16 N + 40) n ncols bytes).  Errors as ld_logdet. */
 ld_status ld_logmv(ld_ctx *ctx, int ncols, const double *V, double *Y, ld_info *info);
 
 /* Q^{-1/2} V for the columns of V (n x ncols, row-major, FP64), by the same contour,

@@ -71,6 +71,10 @@ _lib = None
 
 # ld_matvec_fn: int (*)(void *user, int64_t n, int32_t ncols, const double *P, double *W, void *stream)
 MATVEC_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p)
+# ld_dmatvec_fn: int (*)(void *user, int32_t param, int64_t n, int32_t ncols, const double *X, double *Y,
+#                        void *stream)
+DMATVEC_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int32, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p,
+                         C.c_void_p)
 
 
 def library(build_if_missing: bool = False):
@@ -92,6 +96,7 @@ def library(build_if_missing: bool = False):
         "ld_default_options": ([P(Options)], st),
         "ld_create": ([P(Matrix), C.c_int, C.c_int, dbl, P(Options), P(vp)], st),
         "ld_create_matfree": ([i64, MATVEC_FN, vp, vp, dbl, dbl, C.c_int, dbl, P(Options), P(vp)], st),
+        "ld_matfree_set_derivative": ([vp, DMATVEC_FN, vp, C.c_int], st),
         "ld_set_params": ([vp, dbl, dbl, dbl], st),
         "ld_logdet": ([vp, P(dbl), P(Info)], st),
         "ld_logdet_grad": ([vp, C.c_int, vp, P(dbl), vp, P(Info)], st),
@@ -268,6 +273,28 @@ def ld_create_matfree(n: int, matvec, colouring, lambda_min: float, lambda_max: 
     ctx.matvec_error = None
     ctx_box["ctx"] = ctx
     return ctx
+
+
+def ld_matfree_set_derivative(ctx: Context, dmatvec, n_params: int):
+    """Register dQ/d eta_j for a matrix-free context: dmatvec(j, X, Y) must write
+    Y = (dQ/d eta_j) X (torch float64 CUDA views, as matvec) for j in [0, n_params); then
+    ld_logdet_grad / ld_grad take ids in [0, n_params).  None unregisters.  An exception
+    stops the gradient with LD_ECALLBACK (kept in ctx.matvec_error)."""
+    def call(user, param, n_, ncols, X, Y, stream):
+        try:
+            import torch
+            Xt = torch.as_tensor(_DeviceRows(X, n_, ncols), device="cuda")
+            Yt = torch.as_tensor(_DeviceRows(Y, n_, ncols), device="cuda")
+            with torch.cuda.stream(torch.cuda.ExternalStream(int(stream))):
+                dmatvec(int(param), Xt, Yt)
+            return 0
+        except BaseException as e:   # noqa: BLE001 -- reported through LD_ECALLBACK
+            ctx.matvec_error = e
+            return 1
+
+    fn = DMATVEC_FN(call) if dmatvec is not None else DMATVEC_FN()
+    _check(library().ld_matfree_set_derivative(ctx.handle, fn, None, int(n_params) if dmatvec else 0))
+    ctx._keep.append(fn)
 
 
 def ld_set_params(ctx: Context, kappa2: float, tau: float = 0.0, scale: float = 1.0):

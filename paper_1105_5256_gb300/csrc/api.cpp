@@ -151,7 +151,9 @@ struct ld_ctx {
     cudaGraphExec_t bgraph = nullptr;
     // matrix-free operator (ld_create_matfree): the caller's W = Q P drives the solve
     ld::Matfree *mf = nullptr;
-    std::vector<double> mf_terms;
+    std::vector<double> mf_terms, mf_seeds;
+    void *mf_dfn = nullptr, *mf_duser = nullptr;   // ld_dmatvec_fn and its argument
+    int mf_nparams = 0;
     bool l2_persist = false;   // captured kernels mark the colours persisting in L2
 
     ~ld_ctx() {
@@ -411,7 +413,9 @@ void invalidate_graph(ld_ctx *c) {
 // (tiles g, g + G, ...) iterates on its own stream and one group's end-of-pass
 // reduction and last CTAs overlap the other groups' sweeps.
 ld_status ensure_groups(ld_ctx *c) {
-    const int want = std::min(c->ntiles, (int)ld_ctx::kMaxGroups);
+    // CSR: one group, so that the CTAs of every tile walk the same rows together and the
+    // matrix rows each of them reads come from L2 after the first
+    const int want = c->kind == LD_CSR ? 1 : std::min(c->ntiles, (int)ld_ctx::kMaxGroups);
     if (c->ngroups == want) return LD_OK;
     if (!c->gfork) CUDA_TRY(cudaEventCreateWithFlags(&c->gfork, cudaEventDisableTiming));
     for (int g = 0; g < want; ++g) {
@@ -532,37 +536,83 @@ void fill_info(const ld_ctx *c, ld_info *info, ld_status st, int iters, float ms
     info->rel_resid_max = -1.0;
     info->pass_words = -1;
     if (c->engine == 1 && !c->mf && !c->is_batch)
-        info->pass_words = (lattice2d && c->s.lean ? 4 : 6) + (c->s.keep_x0 ? 2 : 0);
+        info->pass_words = (lattice2d && c->s.lean ? 4 : c->kind == LD_CSR ? 8 : 6) + (c->s.keep_x0 ? 2 : 0);
 }
 
-// matrix-free contexts support ld_logdet, ld_logdet_partial and the getters only
+// entry points a matrix-free context does not support (they need the matrix itself)
 #define REJECT_MATFREE(c)                                                                     \
     do {                                                                                      \
-        if ((c)->mf) return fail(LD_EUNSUPPORTED, "matrix-free context: ld_logdet and "       \
-                                                  "ld_logdet_partial only");                  \
+        if ((c)->mf) return fail(LD_EUNSUPPORTED, "matrix-free context: no matrix to apply, " \
+                                                  "re-parametrise or select a distance on");  \
     } while (0)
 
-// matrix-free solve over colours [cb, ce); out[0] = sum of the terms
-ld_status run_matfree(ld_ctx *c, int cb, int ce, double out[2], ld_info *info) {
+// matrix-free solve over colours [cb, ce); out[0] = sum of the terms, out[1] = sum of the
+// seed projections v^T Q^{-1} v; keep_x keeps the seed solutions for ld_grad
+ld_status run_matfree(ld_ctx *c, int cb, int ce, bool keep_x, double out[2], ld_info *info) {
     Range range("ld matrix-free solve");
     ld::MatfreeStats ms{};
-    std::vector<double> terms(std::max(ce - cb, 0));
+    std::vector<double> terms(std::max(ce - cb, 0)), seeds(terms.size());
     const int max_iter = c->opt.max_iter > 0 ? c->opt.max_iter : 100000;
-    const ld_status st = (ld_status)ld::matfree_solve(c->mf, cb, ce, c->sigma.data(), c->alpha.data(),
-                                                      c->tol, max_iter, c->stream, terms.data(), &ms);
+    ld::MatfreeJob job;
+    job.cb = cb;
+    job.ce = ce;
+    job.n_shifts = c->nshift;
+    job.keep_x = keep_x;
+    c->have_x0 = false;
+    const ld_status st = (ld_status)ld::matfree_solve(c->mf, job, c->sigma.data(), c->alpha.data(), c->tol,
+                                                      max_iter, c->stream, terms.data(), seeds.data(), &ms);
     fill_info(c, info, st, ms.iters, ms.ms, ms.launches, ms.ms, ms.column_iters);
     if (st != LD_OK) return st;
-    double sum = 0.0;
+    double sum = 0.0, ssum = 0.0;
     for (int k = 0; k < ce - cb; ++k) {
         c->mf_terms[cb + k] = terms[k];
+        c->mf_seeds[cb + k] = seeds[k];
         sum += terms[k];
+        ssum += seeds[k];
     }
     if (!std::isfinite(sum)) return fail(LD_ENUMERIC, "non-finite log det");
     out[0] = sum;
-    out[1] = 0.0;
+    out[1] = ssum;
     c->solved = true;
+    c->have_x0 = keep_x;
     c->last_cb = cb;
     c->last_ce = ce;
+    return LD_OK;
+}
+
+// f(Q) V on a matrix-free context: the vector form with the caller's product; yweight
+// pairs with the context's shifts (log: the context's weights)
+ld_status matfree_funmv(ld_ctx *c, int ncols, const double *V, double *Y, ld_info *info,
+                        const std::complex<double> *yweight) {
+    Range range("ld matrix-free vector form");
+    ld::MatfreeStats ms{};
+    std::vector<double> terms(ncols), seeds(ncols);
+    const int max_iter = c->opt.max_iter > 0 ? c->opt.max_iter : 100000;
+    ld::MatfreeJob job;
+    job.rhs = V;
+    job.ncols = ncols;
+    job.yweight = yweight;
+    job.y_out = Y;
+    job.n_shifts = c->nshift;
+    c->have_x0 = false;   // the vector form overwrites the kept seed solutions' buffers
+    const ld_status st = (ld_status)ld::matfree_solve(c->mf, job, c->sigma.data(), c->alpha.data(), c->tol,
+                                                      max_iter, c->stream, terms.data(), seeds.data(), &ms);
+    fill_info(c, info, st, ms.iters, ms.ms, ms.launches, ms.ms, ms.column_iters);
+    return st;
+}
+
+// grad[k] = d log det / d eta_{ids[k]} over the seed solutions kept by the last solve
+ld_status matfree_grad(ld_ctx *c, int n_params, const int *ids, double *grad) {
+    if (!c->have_x0) return fail(LD_EINVAL, "no seed solutions saved: run ld_logdet on a keep_x0 context first");
+    std::vector<double> g(n_params);
+    int rc = 0;
+    const ld_status st = (ld_status)ld::matfree_grad(c->mf, n_params, ids, c->mf_dfn, c->mf_duser, c->stream,
+                                                     g.data(), &rc);
+    if (st != LD_OK) return st;
+    for (int k = 0; k < n_params; ++k) {
+        if (!std::isfinite(g[k])) return fail(LD_ENUMERIC, "non-finite gradient");
+        grad[k] = g[k];
+    }
     return LD_OK;
 }
 
@@ -644,7 +694,8 @@ ld_status run_solve(ld_ctx *c, int cb, int ce, bool keep_x0, double out[2], ld_i
             CUDA_TRY(cudaEventRecord(c->ev2, c->stream));
             CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
             CUDA_TRY(cudaEventRecord(c->ev3, c->stream));
-            launches += (int64_t)c->chunk * std::max(c->ngroups, 1);
+            // one launch per tile group and pass (two on CSR: the step and the product)
+            launches += (int64_t)c->chunk * std::max(c->ngroups, 1) * (c->kind == LD_CSR ? 2 : 1);
             done_iters += c->chunk;
             CUDA_TRY(cudaMemcpyAsync(c->h_pinned, c->s.remaining, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
             CUDA_TRY(cudaMemcpyAsync(c->h_pinned + 1, c->s.status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
@@ -741,6 +792,23 @@ std::string tune_key(const ld_matrix *Q, int precision, int lattice_pass, int nc
     k << Q->kind << ":" << precision << (lattice_pass ? "w" : "") << ":" << (Q->periodic ? 1 : 0) << ":" << Q->dims[0] << "x"
       << Q->dims[1] << "x" << (Q->kind == LD_STENCIL_3D7 ? Q->dims[2] : 1) << ":" << ncolours
       << (Q->kappa2_field ? ":field" : "") << (Q->obs_mask ? ":mask" : "");
+    if (Q->kind == LD_CSR) {
+        // a CSR pattern: its size and an FNV-1a hash of 64 sampled row starts and indices
+        const int64_t n = Q->n, nnz = Q->rowptr[n];
+        uint64_t h = 1469598103934665603ull;
+        auto mix = [&h](int64_t v) {
+            for (int b = 0; b < 8; ++b) {
+                h ^= (uint64_t)((v >> (8 * b)) & 0xff);
+                h *= 1099511628211ull;
+            }
+        };
+        for (int q = 0; q < 64; ++q) {
+            const int64_t i = n * q / 64;
+            mix(Q->rowptr[i]);
+            if (nnz > 0) mix(Q->colidx[std::min<int64_t>(nnz - 1, Q->rowptr[i])]);
+        }
+        k << ":csr" << n << "/" << nnz << "/" << std::hex << h;
+    }
     return k.str();
 }
 
@@ -782,7 +850,7 @@ void tune_save_locked() {
 }
 
 int autotune_tile(const ld_matrix *Q, int d, int N, double tol, const ld_options &opt,
-                  const std::vector<int32_t> &colour, int ncolours) {
+                  const std::vector<int32_t> &colour, int ncolours, double csr_lmin, double csr_lmax) {
     const std::string key = tune_key(Q, opt.precision, opt.lattice_pass, ncolours);
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -812,6 +880,10 @@ int autotune_tile(const ld_matrix *Q, int d, int N, double tol, const ld_options
             sub.chunk_iters = 8;
             sub.engine = 1;
             sub.keep_x0 = kx;
+            if (Q->kind == LD_CSR && !(sub.lambda_min > 0.0 && sub.lambda_max > 0.0)) {
+                sub.lambda_min = csr_lmin;   // the interval the context computed once
+                sub.lambda_max = csr_lmax;
+            }
             ld_ctx *t = nullptr;
             if (ld_create(Q, d, N, tol, &sub, &t) != LD_OK) {
                 ok = false;
@@ -844,6 +916,13 @@ int autotune_tile(const ld_matrix *Q, int d, int N, double tol, const ld_options
 
 ld_status check_params(const ld_ctx *c, int n_params, const int *ids) {
     if (n_params < 1 || n_params > 3 || !ids) return fail(LD_EINVAL, "n_params must be 1..3 with ids");
+    if (c->mf) {   // the caller's parameters of ld_matfree_set_derivative
+        if (!c->mf_dfn) return fail(LD_EINVAL, "matrix-free context without ld_matfree_set_derivative");
+        for (int k = 0; k < n_params; ++k)
+            if (ids[k] < 0 || ids[k] >= c->mf_nparams)
+                return fail(LD_EINVAL, "parameter id %d outside [0, %d)", ids[k], c->mf_nparams);
+        return LD_OK;
+    }
     for (int k = 0; k < n_params; ++k) {
         const int p = ids[k];
         if (p < LD_P_KAPPA2 || p > LD_P_SCALE) return fail(LD_EINVAL, "unknown parameter id %d", p);
@@ -942,8 +1021,9 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
     }
     // tiling: explicit, autotuned (large multi-CTA problems), or the padding rule
     c->T = -1;
-    if (opt.tile_width == 0 && opt.engine != 2 && c->n >= 65536 && c->kind != LD_CSR)
-        c->T = autotune_tile(Q, colouring_distance, n_shifts, tol, opt, c->colour, c->ncolours);
+    if (opt.tile_width == 0 && opt.engine != 2 && c->n >= 65536)
+        c->T = autotune_tile(Q, colouring_distance, n_shifts, tol, opt, c->colour, c->ncolours, c->csr_lmin,
+                             c->csr_lmax);
     if (c->T < 0) c->T = choose_tile(opt.precision, c->ncolours, opt.tile_width);
     if (c->T < 0) return fail(LD_EINVAL, "tile_width %d not available for this precision", opt.tile_width);
     c->ntiles = (c->ncolours + c->T - 1) / c->T;
@@ -1118,6 +1198,7 @@ ld_status ld_create_matfree(int64_t n, ld_matvec_fn matvec, void *user, const in
     c->T = 0;
     c->engine = 3;
     c->mf_terms.assign(c->ncolours, 0.0);
+    c->mf_seeds.assign(c->ncolours, 0.0);
     c->lmin = lambda_min;
     c->lmax = lambda_max;
     c->sigma.assign(n_shifts, 0.0);
@@ -1137,6 +1218,22 @@ ld_status ld_create_matfree(int64_t n, ld_matvec_fn matvec, void *user, const in
         return fail(e == (int)cudaErrorMemoryAllocation ? LD_ENOMEM : LD_ECUDA, "matrix-free buffers: %s",
                     cudaGetErrorString((cudaError_t)e));
     *out = guard.release();
+    return LD_OK;
+}
+
+ld_status ld_matfree_set_derivative(ld_ctx *c, ld_dmatvec_fn dmatvec, void *user, int n_params) {
+    if (!c) return fail(LD_EINVAL, "ctx is NULL");
+    if (!c->mf) return fail(LD_EINVAL, "not a matrix-free context");
+    if (!dmatvec) {
+        c->mf_dfn = nullptr;
+        c->mf_duser = nullptr;
+        c->mf_nparams = 0;
+        return LD_OK;
+    }
+    if (n_params < 1 || n_params > 3) return fail(LD_EINVAL, "n_params must be in [1, 3]");
+    c->mf_dfn = reinterpret_cast<void *>(dmatvec);
+    c->mf_duser = user;
+    c->mf_nparams = n_params;
     return LD_OK;
 }
 
@@ -1172,7 +1269,7 @@ ld_status ld_logdet(ld_ctx *c, double *logdet, ld_info *info) {
     if (!c || !logdet) return fail(LD_EINVAL, "ctx and logdet must be non-NULL");
     if (c->is_batch) return fail(LD_EINVAL, "batched context: use ld_batch_logdet");
     double out[2];
-    ld_status st = c->mf ? run_matfree(c, 0, c->ncolours, out, info)
+    ld_status st = c->mf ? run_matfree(c, 0, c->ncolours, c->opt.keep_x0 != 0, out, info)
                          : run_solve(c, 0, c->ncolours, c->opt.keep_x0 != 0, out, info);
     if (st == LD_OK) *logdet = out[0];
     return st;
@@ -1181,8 +1278,8 @@ ld_status ld_logdet(ld_ctx *c, double *logdet, ld_info *info) {
 ld_status ld_grad(ld_ctx *c, int n_params, const int *ids, double *grad) {
     if (!c || !grad) return fail(LD_EINVAL, "ctx and grad must be non-NULL");
     if (c->is_batch) return fail(LD_EINVAL, "batched context: use ld_batch_logdet");
-    REJECT_MATFREE(c);
     if (ld_status v = check_params(c, n_params, ids)) return v;
+    if (c->mf) return matfree_grad(c, n_params, ids, grad);
     if (!c->have_x0) return fail(LD_EINVAL, "no seed solutions saved: run ld_logdet on a keep_x0 context first");
     double *d_out = c->s.result + 2;
     ENGINE_TRY(ld::engine_grad_params(c->s, n_params, ids, d_out, c->stream));
@@ -1191,7 +1288,8 @@ ld_status ld_grad(ld_ctx *c, int n_params, const int *ids, double *grad) {
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     for (int k = 0; k < n_params; ++k) {
         if (!std::isfinite(h[k])) return fail(LD_ENUMERIC, "non-finite gradient");
-        grad[k] = h[k];
+        // a CSR matrix holds s Q0: its kernel summed (Q v)^T x, d/ds takes Q0 = Q / s
+        grad[k] = c->kind == LD_CSR ? h[k] / c->scale : h[k];
     }
     return LD_OK;
 }
@@ -1200,8 +1298,16 @@ ld_status ld_logdet_grad(ld_ctx *c, int n_params, const int *ids, double *logdet
                          ld_info *info) {
     if (!c || !logdet || !grad) return fail(LD_EINVAL, "ctx, logdet and grad must be non-NULL");
     if (c->is_batch) return fail(LD_EINVAL, "batched context: use ld_batch_logdet");
-    REJECT_MATFREE(c);
     if (ld_status v = check_params(c, n_params, ids)) return v;
+    if (c->mf) {
+        double out[2];
+        ld_status st = run_matfree(c, 0, c->ncolours, true, out, info);
+        if (st != LD_OK) return st;
+        if (ld_status g = matfree_grad(c, n_params, ids, grad)) return g;
+        if (info) info->gpu_launches += 2 * n_params;
+        *logdet = out[0];
+        return LD_OK;
+    }
     // d/d kappa2 of a scalar-kappa2 5/7-point grid is tr(Q^{-1}) * scale: the projected
     // seed sum v^T Q^{-1} v needs no stored seed vectors.
     bool projected = (c->kind == LD_STENCIL_2D5 || c->kind == LD_STENCIL_3D7) && !c->has_field;
@@ -1225,7 +1331,7 @@ ld_status ld_logdet_partial(ld_ctx *c, int cb, int ce, double *partial, ld_info 
     if (c->is_batch) return fail(LD_EINVAL, "batched context: use ld_batch_logdet");
     if (cb < 0 || ce < cb || ce > c->ncolours) return fail(LD_EINVAL, "colour range [%d, %d) outside [0, %d)", cb, ce, c->ncolours);
     double out[2];
-    ld_status st = c->mf ? run_matfree(c, cb, ce, out, info)
+    ld_status st = c->mf ? run_matfree(c, cb, ce, c->opt.keep_x0 != 0, out, info)
                          : run_solve(c, cb, ce, c->opt.keep_x0 != 0, out, info);
     if (st == LD_OK) *partial = out[0];
     return st;
@@ -1235,10 +1341,10 @@ ld_status ld_column_terms(const ld_ctx *c, double *terms, double *seed) {
     if (!c || !terms) return fail(LD_EINVAL, "ctx and terms must be non-NULL");
     if (c->is_batch) return fail(LD_EINVAL, "batched context: use ld_batch_logdet");
     if (!c->solved) return fail(LD_EINVAL, "no completed solve on this context");
-    if (c->mf) {   // the seed system is not followed: its projections are NaN
+    if (c->mf) {
         for (int k = 0; k < c->ncolours; ++k) {
             terms[k] = c->mf_terms[k];
-            if (seed) seed[k] = NAN;
+            if (seed) seed[k] = c->mf_seeds[k];
         }
         return LD_OK;
     }
@@ -1420,16 +1526,23 @@ static ld_status funmv(ld_ctx *c, int ncols, const double *V, double *Y, ld_info
 
 ld_status ld_logmv(ld_ctx *c, int ncols, const double *V, double *Y, ld_info *info) {
     if (!c) return fail(LD_EINVAL, "bad arguments");
+    if (c->mf) {
+        if (!V || !Y || ncols < 1) return fail(LD_EINVAL, "bad arguments");
+        return matfree_funmv(c, ncols, V, Y, info, c->alpha.data());
+    }
     return funmv(c, ncols, V, Y, info, c->s.weight);
 }
 
 ld_status ld_invsqrt_mv(ld_ctx *c, int ncols, const double *V, double *Y, ld_info *info) {
     if (!c) return fail(LD_EINVAL, "bad arguments");
     if (c->is_batch) return fail(LD_EINVAL, "batched context");
-    REJECT_MATFREE(c);
     std::vector<std::complex<double>> sg(c->nshift), be(c->nshift);
     if (ld::hht_invsqrt_nodes(c->lmin, c->lmax, c->nshift, sg.data(), be.data()) != 0)
         return fail(LD_EINVAL, "bad spectral interval [%g, %g]", c->lmin, c->lmax);
+    if (c->mf) {   // the same poles as the log nodes, so the context's shifts serve
+        if (!V || !Y || ncols < 1) return fail(LD_EINVAL, "bad arguments");
+        return matfree_funmv(c, ncols, V, Y, info, be.data());
+    }
     std::vector<double2> hw(c->nshift);
     for (int l = 0; l < c->nshift; ++l) hw[l] = make_double2(be[l].real(), be[l].imag());
     DevBuf wd;

@@ -542,10 +542,12 @@ __device__ double grad_row(const Solve &s, int pid, int64_t i) {
     const Operator &op = s.op;
     const int ci = s.colour[i];
     if (op.kind == KIND_CSR) {
+        // scale: E = Q0 = Q / s; the values on the device are Q's (scaled), so this sums
+        // (Q v)^T x and the caller divides by s
         if (pid != 2) return 0.0;
         double g = 0.0;
         for (int64_t e = op.rowptr[i]; e < op.rowptr[i + 1]; ++e)
-            g += op.val_d[e] / op.scale * x0_at<V>(s, i, s.colour[op.colidx[e]]);
+            g += op.val_d[e] * x0_at<V>(s, i, s.colour[op.colidx[e]]);
         return g;
     }
     const int nx = op.nx, ny = op.ny, nz = op.nz;
@@ -789,7 +791,7 @@ int engine_plan(Solve &s) {
     // one resident wave; with several tiles (tile groups run concurrently on their own
     // streams) 1.5 waves, so that CTAs of one group fill the gaps of another
     int64_t target = (int64_t)sms * occ;
-    if (s.ntiles >= 2) target = target * 3 / 2;
+    if (s.ntiles >= 2 && s.op.kind != KIND_CSR) target = target * 3 / 2;
     s.strips = 1;
     s.seg = 1;
     if (lattice2d) {
@@ -819,6 +821,8 @@ int engine_plan(Solve &s) {
         s.bpt = (int)(s.strips * nsegs);
         return s.bpt;
     }
+    // CSR: one resident wave over all tiles (one tile group), CTA x of every tile on the
+    // same rows at the same time
     int64_t bpt = target / s.ntiles;
     const int64_t need = (s.op.n + 255) / 256;
     if (bpt > need) bpt = need;

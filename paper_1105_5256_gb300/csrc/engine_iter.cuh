@@ -1,6 +1,7 @@
 // Launch and occupancy of the per-iteration pass kernels, instantiated per
 // precision by engine_iter_f32.cu and engine_iter_f64.cu.
 #pragma once
+#include "engine_csr.cuh"
 #include "engine_device.cuh"
 #include "engine_lean.cuh"
 
@@ -77,8 +78,9 @@ struct IterLauncher {
                 k_stream3d<V, T, true><<<grid, P3T, stream3d_smem_bytes<V, T>(), st>>>(s, cur);
             else
                 k_stream3d<V, T, false><<<grid, P3T, stream3d_smem_bytes<V, T>(), st>>>(s, cur);
-        } else {
-            k_pass<V, T, KIND><<<grid, 256, 0, st>>>(s, cur);
+        } else {   // CSR: the streaming step, then the product with the dots and the tail
+            k_csr_step<V, T><<<grid, CSR_NT, 0, st>>>(s, cur);
+            k_csr_spmv<V, T><<<grid, CSR_NT, 0, st>>>(s, cur);
         }
         return (int)cudaGetLastError();
     }
@@ -120,7 +122,7 @@ struct OccLauncher {
                 return (int)cudaGetLastError();
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_stream3d<V, T, true>, P3T, sm);
         } else {
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pass<V, T, KIND>, 256, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_csr_spmv<V, T>, CSR_NT, 0);
         }
         (void)b;
         *out = a;

@@ -166,11 +166,26 @@ struct MatfreeStats {
 // fn is an ld_matvec_fn; colour (host, n entries in [0, C)) is copied; 0 or a CUDA error
 int matfree_create(Matfree **out, int64_t n, const int32_t *colour, int C, int N, void *fn, void *user);
 void matfree_destroy(Matfree *m);
-// colours [cb, ce): terms_out[c - cb] = Re sum_l weight_l v_c^T (Q - sigma_l I)^{-1} v_c;
-// returns an ld_status (message through set_last_error)
-int matfree_solve(Matfree *m, int cb, int ce, const std::complex<double> *sigma,
+// one solve: the probing vectors of colours [cb, ce), or (rhs != nullptr) ncols given
+// right-hand sides with the vector form y = Re sum_l yweight_l (Q - sigma_l I)^{-1} v
+struct MatfreeJob {
+    int cb = 0, ce = 0;
+    const double *rhs = nullptr;                     // host, n x ncols row-major
+    int ncols = 0;
+    const std::complex<double> *yweight = nullptr;   // host, n_shifts (nullptr: the log weights)
+    double *y_out = nullptr;                         // host, n x ncols
+    int n_shifts = 0;
+    bool keep_x = false;                             // keep the seed solutions for matfree_grad
+};
+// terms_out[c] = Re sum_l weight_l v_c^T (Q - sigma_l I)^{-1} v_c, seeds_out[c] = v_c^T
+// Q^{-1} v_c (nullable); returns an ld_status (message through set_last_error)
+int matfree_solve(Matfree *m, const MatfreeJob &job, const std::complex<double> *sigma,
                   const std::complex<double> *weight, double tol, int max_iter, cudaStream_t stream,
-                  double *terms_out, MatfreeStats *st);
+                  double *terms_out, double *seeds_out, MatfreeStats *st);
+// grad[k] = sum_c v_c^T (dQ/d eta_{ids[k]}) x_c over the seed solutions kept by the last
+// probing solve (dfn an ld_dmatvec_fn); LD_EINVAL when none are kept
+int matfree_grad(Matfree *m, int n_params, const int *ids, void *dfn, void *duser, cudaStream_t stream,
+                 double *grad, int *callback_rc);
 
 // host: P1 finite-element SPDE precision of a triangulation as sorted CSR (fem.cpp);
 // 0, or -1 vertex index out of range, -2 degenerate triangle, -3 vertex in no triangle

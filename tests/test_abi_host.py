@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(lib):
     assert len(syms) >= 20
     for s in syms:
         assert hasattr(lib, s), s
-    assert lib.ld_abi_version() == 5
+    assert lib.ld_abi_version() == 6
 
 
 @pytest.mark.parametrize("kind,dims,per,d", [
@@ -238,6 +238,12 @@ def test_matfree_create_checks_arguments_before_any_device_call(lib):
         with pytest.raises(L.LogDetError) as e:
             L.ld_create_matfree(**args)
         assert e.value.status == status, kw
+
+
+def test_matfree_derivative_setter_rejects_a_null_context(lib):
+    """ld_matfree_set_derivative checks its context on the host."""
+    fn = L.DMATVEC_FN(lambda *a: 0)
+    assert lib.ld_matfree_set_derivative(None, fn, None, 1) == L.LD_EINVAL
 
 
 def test_batch_create_checks_every_instance_on_the_host(lib):
