@@ -272,7 +272,7 @@ def config_periodic64(L, steps):
             "roofline": {"bound": "latency", "note": "the 4096-vertex problem is L2-resident; one CTA per tile"}}
 
 
-def config_field3d(L, side, steps, peak, src, fp64=True):
+def config_field3d(L, side, steps, peak, src, fp64=True, T=0):
     """configs[4]: Dirichlet side^3, 7-point, seeded kappa^2 field (log kappa^2 = -2 +
     smoothed N(0,1)), distance 6, N = 32, tol 1e-6, mixed precision; one evaluation = log
     det and its derivative with respect to the field's scale c (kappa^2 = c kappa0^2)."""
@@ -280,12 +280,14 @@ def config_field3d(L, side, steps, peak, src, fp64=True):
     n = side ** 3
     field = synth.kappa2_field(5, dims)
     ctx = L.ld_create(L.grid_matrix(L.LD_STENCIL_3D7, dims, 1.0, kappa2_field=field), 6, 32, 1e-6,
-                      L.options(precision=L.LD_MIXED))
+                      L.options(precision=L.LD_MIXED, tile_width=T))
     timed_evals(L, ctx, 1, grad=[L.LD_P_KAPPA2])
     r = timed_evals(L, ctx, steps, grad=[L.LD_P_KAPPA2])
     info = r["info"]
     T = info["tile_width"]
-    roof = roofline_entry("k_stream3d (7-point, stored w, seed solution kept)", n, T, 4, r, True, 4 * n, peak, src)
+    lean = r["info"]["pass_words"] == 6
+    roof = roofline_entry("k_lean3d (7-point, lean, seed solution kept)" if lean else
+                          "k_stream3d (7-point, stored w, seed solution kept)", n, T, 4, r, True, 4 * n, peak, src)
     out = {"workload": "Dirichlet %d^3, 7-point, kappa^2 field, d=6, N=32, tol 1e-6, grad c" % side,
            "value": steps / (r["ms"] / 1e3), "unit": UNIT, "evaluations": steps,
            "dtype": "f32 vectors / f64 scalars", "n_colours": info["n_colours"], "tile_width": T,
@@ -405,16 +407,28 @@ def run_batch(args):
     mats = [L.grid_matrix(i.kind, i.dims, i.kappa2) for i in insts]
     dists = [i.distance for i in insts]
     out = {}
+    peak, src = peak_hbm()
     for name, prec in (("mixed", L.LD_MIXED), ("fp64", L.LD_FP64)):
         b = L.ld_batch_create(mats, dists, NSHIFT, TOL, L.options(precision=prec))
         for _ in range(args.warmup):
             L.ld_batch_logdet(b)
         ms = 0.0
+        vti = 0
         for _ in range(args.steps):
             vals, _, info = L.ld_batch_logdet(b)
             ms += info["ms"]
+            vti += info["vertex_tile_iters"]
+        word = 4 if prec == L.LD_MIXED else 8
+        # the active bytes: 4 state words a vertex and column of every pass each tile ran
+        alg = 4 * word * info["tile_width"] * vti
+        achieved = alg / (ms / 1e3) / 1e9
         out[name] = {"value": 256 * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
-                     "vals": vals, "tile_width": info["tile_width"]}
+                     "vals": vals, "tile_width": info["tile_width"],
+                     "roofline": {"bound": "hbm", "kernel": "k_batch_solve + grid engine (large instances)",
+                                  "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                                  "traffic": None, "algorithmic_bytes_per_step": alg / args.steps,
+                                  "peak_source": src,
+                                  "note": "whole batch wall time, both engines, over the active bytes"}}
         del b
     # 256 sequential FP64 evaluations, one context per instance (created beforehand)
     ctxs = [L.ld_create(m, d, NSHIFT, TOL, L.options(precision=L.LD_FP64)) for m, d in zip(mats, dists)]
@@ -435,8 +449,9 @@ def run_batch(args):
             "dtype": "f32 vectors / f64 scalars", "data": "synthetic (seeded batch)",
             "config": {"workload": "256 grids, sides U{32..512}, 5-pt d=4 / 13-pt d=2, N=20, tol 1e-6",
                        "points": int(sum(i.n for i in insts)), "tile_width": out["mixed"]["tile_width"]},
+            "roofline": out["mixed"]["roofline"],
             "fp64_form": {"value": out["fp64"]["value"], "ms_per_step": out["fp64"]["ms_per_step"],
-                          "mixed_vs_fp64_rel_diff_max": rel},
+                          "mixed_vs_fp64_rel_diff_max": rel, "roofline": out["fp64"]["roofline"]},
             "sequential_fp64": {"value": 256 / (seq_ms / 1e3), "ms": seq_ms,
                                 "note": "256 separate ld_logdet calls in FP64, one context per instance",
                                 "mixed_batch_vs_sequential_rel_diff_max": rel_seq}}
@@ -488,7 +503,7 @@ def run_field3d(args):
     clocks = Clocks()
     clocks.start()
     t0 = time.perf_counter()
-    r = config_field3d(L, args.side, args.steps, peak, src, fp64=True)
+    r = config_field3d(L, args.side, args.steps, peak, src, fp64=args.fp64_sample > 0, T=args.tile_width)
     wall = time.perf_counter() - t0
     clk = clocks.stop()
     line = {"metric": "log-det+grad evals/sec (Dirichlet %d^3, 7-point, kappa^2 field, d=6, N=32)" % args.side,

@@ -147,6 +147,10 @@ typedef struct {
                                  pass (r, Q p, p), 8 for the CSR pass (its step, then its
                                  product re-reads r and p), plus 2 when the pass also updates
                                  the kept seed solution; -1 for the other engines */
+    int64_t vertex_tile_iters; /* sum over tiles of vertices x the iterations the tile ran
+                                 (a batch: over every instance's tiles; a matrix-free context:
+                                 over columns): the CG state a solve streams is 4 words per
+                                 vertex and column of a pass, so 4 x word x T x this bytes */
 } ld_info;
 
 /* ABI version (LD_ABI_VERSION).  Never fails. */

@@ -61,7 +61,7 @@ class Info(C.Structure):
                 ("ms", C.c_double), ("iter_ms", C.c_double), ("tile_iters", C.c_int64),
                 ("gpu_launches", C.c_int64), ("bulk_rows", C.c_int32),
                 ("reliable_updates", C.c_int32), ("rel_resid_max", C.c_double),
-                ("pass_words", C.c_int32)]
+                ("pass_words", C.c_int32), ("vertex_tile_iters", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -19,7 +19,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["engine.cu", "engine_iter_f32.cu", "engine_iter_f64.cu", "static_scratch.cu", "matfree.cu"]
 CXX_SOURCES = ["api.cpp", "bounds.cpp", "colouring.cpp", "fem.cpp", "hht.cpp"]
-HEADERS = ["internal.h", "engine_device.cuh", "engine_iter.cuh", "engine_lean.cuh", "engine_csr.cuh"]
+HEADERS = ["internal.h", "engine_device.cuh", "engine_iter.cuh", "engine_lean.cuh", "engine_csr.cuh",
+           "engine_lean3d.cuh"]
 
 
 def _cuda_home() -> str:

@@ -519,6 +519,7 @@ void fill_info(const ld_ctx *c, ld_info *info, ld_status st, int iters, float ms
     if (!info) return;
     info->iter_ms = iter_ms;
     info->tile_iters = tile_iters;
+    info->vertex_tile_iters = c->n * tile_iters;
     info->status = st;
     info->n_colours = c->ncolours;
     info->n_shifts = c->nshift;
@@ -536,7 +537,7 @@ void fill_info(const ld_ctx *c, ld_info *info, ld_status st, int iters, float ms
     info->rel_resid_max = -1.0;
     info->pass_words = -1;
     if (c->engine == 1 && !c->mf && !c->is_batch)
-        info->pass_words = (lattice2d && c->s.lean ? 4 : c->kind == LD_CSR ? 8 : 6) + (c->s.keep_x0 ? 2 : 0);
+        info->pass_words = (c->s.lean ? 4 : c->kind == LD_CSR ? 8 : 6) + (c->s.keep_x0 ? 2 : 0);
 }
 
 // entry points a matrix-free context does not support (they need the matrix itself)
@@ -660,12 +661,13 @@ ld_status run_solve(ld_ctx *c, int cb, int ce, bool keep_x0, double out[2], ld_i
         c->s.lean = want_lean;
         ld::engine_plan(c->s);           // the lean plan's occupancy depends on keep_x0
         c->lean_plan_x0 = want_x0;
-        if (want_lean && !c->lane_built) {
+        const bool codes = want_lean && c->kind != LD_STENCIL_3D7;   // the 3D pass reads colours
+        if (codes && !c->lane_built) {
             CUDA_TRY(c->d_lane.alloc(ld::engine_lean_code_bytes(c->s)));
             ENGINE_TRY(ld::engine_lean_codes(c->s, c->d_lane.as<uint8_t>(), c->stream));
             c->lane_built = true;
         }
-        c->s.lane = want_lean ? c->d_lane.as<uint8_t>() : nullptr;
+        c->s.lane = codes ? c->d_lane.as<uint8_t>() : nullptr;
         invalidate_graph(c);
     }
     c->have_x0 = false;
@@ -1812,7 +1814,7 @@ ld_status batch_build(int count, const ld_matrix *Qs, const int *distances, int 
         CUDA_TRY(cudaMemcpy(c->d_items.p, hitems.data(), sizeof(int2) * hitems.size(), cudaMemcpyHostToDevice));
         CUDA_TRY(c->d_queue.alloc(sizeof(int)));
         CUDA_TRY(c->d_bout.alloc(sizeof(double) * 2 * nsmall));
-        CUDA_TRY(c->d_bint.alloc(sizeof(int) * 3 * nsmall));
+        CUDA_TRY(c->d_bint.alloc(sizeof(int) * 4 * nsmall));   // flags, iters, colours, tile passes
         CUDA_TRY(cudaMemcpy(c->d_bint.as<int>() + 2 * nsmall, ncol.data(), sizeof(int) * nsmall, cudaMemcpyHostToDevice));
         int dev = 0, sms = 152;
         CUDA_TRY(cudaGetDevice(&dev));
@@ -1827,7 +1829,8 @@ ld_status batch_build(int count, const ld_matrix *Qs, const int *distances, int 
                                          c->d_items.as<int2>(), c->nitems, c->d_queue.as<int>(), max_iter,
                                          opt.precision == LD_MIXED ? 1 : 0, c->T, c->bgrid,
                                          c->d_bout.as<double>(), c->d_bout.as<double>() + nsmall,
-                                         c->d_bint.as<int>(), c->d_bint.as<int>() + nsmall, c->stream);
+                                         c->d_bint.as<int>(), c->d_bint.as<int>() + nsmall,
+                                         c->d_bint.as<int>() + 3 * nsmall, c->stream);
         cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
         if (err) {
             if (g) cudaGraphDestroy(g);
@@ -1942,14 +1945,14 @@ ld_status ld_batch_logdet(ld_ctx *c, double *logdets, double *grads, ld_info *in
     const int count = (int)c->subs.size();
     const int nsmall = (int)c->small_idx.size();
     std::vector<double> out(2 * std::max(nsmall, 1));
-    std::vector<int> flags(2 * std::max(nsmall, 1));
+    std::vector<int> flags(4 * std::max(nsmall, 1));
     const auto t0 = std::chrono::steady_clock::now();
     // the persistent launch for the small instances first (asynchronous) ...
     if (nsmall > 0) CUDA_TRY(cudaGraphLaunch(c->bgraph, c->stream));
     // ... then the large ones, each across the GPU on its own stream
     std::vector<double> lval(c->large_idx.size()), lseed(c->large_idx.size());
     int iters = 0;
-    int64_t tile_iters = 0, launches = nsmall > 0 ? 3 : 0;
+    int64_t tile_iters = 0, vertex_tile_iters = 0, launches = nsmall > 0 ? 3 : 0;
     ld_status st = LD_OK;
     for (size_t k = 0; k < c->large_idx.size() && st == LD_OK; ++k) {
         ld_ctx *sc = c->subs[c->large_idx[k]];
@@ -1966,17 +1969,19 @@ ld_status ld_batch_logdet(ld_ctx *c, double *logdets, double *grads, ld_info *in
         lseed[k] = o[1];
         iters = std::max(iters, (int)si.iters);
         tile_iters += si.tile_iters;
+        vertex_tile_iters += si.vertex_tile_iters;
         launches += si.gpu_launches;
     }
     if (nsmall > 0) {
         CUDA_TRY(cudaMemcpyAsync(out.data(), c->d_bout.p, sizeof(double) * 2 * nsmall, cudaMemcpyDeviceToHost, c->stream));
-        CUDA_TRY(cudaMemcpyAsync(flags.data(), c->d_bint.p, sizeof(int) * 2 * nsmall, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(flags.data(), c->d_bint.p, sizeof(int) * 4 * nsmall, cudaMemcpyDeviceToHost, c->stream));
     }
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     for (int k = 0; k < nsmall && st == LD_OK; ++k) {
         iters = std::max(iters, flags[nsmall + k]);
-        tile_iters += (int64_t)c->subs[c->small_idx[k]]->ntiles * flags[nsmall + k];
+        tile_iters += flags[3 * nsmall + k];
+        vertex_tile_iters += c->subs[c->small_idx[k]]->n * flags[3 * nsmall + k];
         const int f = flags[k];
         if (f == 0) continue;
         const int i = c->small_idx[k];
@@ -1996,7 +2001,8 @@ ld_status ld_batch_logdet(ld_ctx *c, double *logdets, double *grads, ld_info *in
         info->gpu_launches = launches;
         info->bulk_rows = -1;
         info->rel_resid_max = -1.0;
-        info->tile_iters = tile_iters;   // upper bound: every tile counted at its instance's iterations
+        info->tile_iters = tile_iters;
+        info->vertex_tile_iters = vertex_tile_iters;
         info->n_colours = 0;
         for (ld_ctx *sc : c->subs) info->n_colours += sc->ncolours;
     }

@@ -3,6 +3,7 @@
 // vector form (log(Q) V), operator application, gradients (sm_103a).
 #include "engine_device.cuh"
 #include "engine_lean.cuh"
+#include "engine_lean3d.cuh"
 
 namespace ld {
 
@@ -188,7 +189,7 @@ __global__ void k_batch_prep(const Solve *solves, int count) {
 
 // per instance (fixed column order): log det, the projected seed sum, convergence flag
 __global__ void k_batch_finish(const Solve *solves, const int *ncolours, int count, double *logdet,
-                               double *seed, int *flag, int *iters) {
+                               double *seed, int *flag, int *iters, int *tile_passes) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
         const Solve &s = solves[i];
         double a = 0.0, b = 0.0;
@@ -201,6 +202,14 @@ __global__ void k_batch_finish(const Solve *solves, const int *ncolours, int cou
         logdet[i] = a;
         seed[i] = b;
         iters[i] = it;
+        // passes the instance's tiles ran: a tile runs until its last column stops
+        int tp = 0;
+        for (int t = 0; t < s.ntiles; ++t) {
+            int m = 0;
+            for (int k = 0; k < s.T; ++k) m = max(m, s.col_iters[t * s.T + k]);
+            tp += m;
+        }
+        tile_passes[i] = tp;
         flag[i] = *s.status != 0 ? *s.status : (*s.remaining > 0 ? -1 : 0);
     }
 }
@@ -704,8 +713,10 @@ struct ApplyLauncher {
 
 int engine_lean_x(const Solve &s, bool keep_x0) {
     const int k = s.op.kind;
-    if (s.precision != 1 || (k != KIND_2D5 && k != KIND_2D13_SQ) || (s.T != 2 && s.T != 4)) return 0;
+    if (s.precision != 1 || (k != KIND_2D5 && k != KIND_2D13_SQ && k != KIND_3D7) || (s.T != 2 && s.T != 4))
+        return 0;
     if (s.asig) return 0;                               // shifted-vector mode reads w
+    if (k == KIND_3D7) return LEAN_3D;
     if (k == KIND_2D13_SQ && keep_x0) return 0;         // the Matern state holds no p
     // two columns a thread at T = 2 on even widths (16-byte aligned pairs), else one
     return s.T == 2 && s.op.nx % 2 == 0 ? 2 : 1;
@@ -779,7 +790,9 @@ int engine_plan(Solve &s) {
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const bool lattice2d = s.op.kind == KIND_2D5 || s.op.kind == KIND_2D13_SQ;
-    if (!lattice2d || s.precision != 1 || s.asig) s.lean = 0;   // shifted-vector mode reads w
+    const bool lean3d = s.op.kind == KIND_3D7 && s.lean == LEAN_3D && s.precision == 1 && !s.asig &&
+                        (s.T == 2 || s.T == 4);
+    if ((!lattice2d && !lean3d) || s.precision != 1 || s.asig) s.lean = 0;   // shifted-vector mode reads w
     // bulk row copies measured faster for packs of 24 bytes and more; per-thread
     // copies win for 8- and 16-byte packs (fewer instructions on the critical path)
     const int pack_bytes = s.T * (s.precision == 0 ? (int)sizeof(double) : (int)sizeof(float));
@@ -811,7 +824,8 @@ int engine_plan(Solve &s) {
     }
     if (s.op.kind == KIND_3D7) {
         // one CTA per (x-y tile, z segment); segments only when the x-y tiles are too few
-        const int tx = (s.op.nx + P3X - 3) / (P3X - 2), ty = (s.op.ny + P3Y - 3) / (P3Y - 2);
+        const int tx = lean3d ? (s.op.nx + L3_OWNX - 1) / L3_OWNX : (s.op.nx + P3X - 3) / (P3X - 2);
+        const int ty = lean3d ? (s.op.ny + L3_OWNY - 1) / L3_OWNY : (s.op.ny + P3Y - 3) / (P3Y - 2);
         s.strips = tx * ty;
         int64_t nsegs = target / ((int64_t)s.strips * s.ntiles);
         if (nsegs < 1) nsegs = 1;
@@ -862,7 +876,8 @@ int engine_batch_occupancy(int precision, int T) {
 
 int engine_batch(const Solve *solves_dev, const int *ncolours_dev, int count, const int2 *items_dev,
                  int nitems, int *queue_dev, int max_iter, int precision, int T, int grid,
-                 double *logdet_dev, double *seed_dev, int *flag_dev, int *iters_dev, void *stream) {
+                 double *logdet_dev, double *seed_dev, int *flag_dev, int *iters_dev, int *tile_passes_dev,
+                 void *stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int e = (int)cudaMemsetAsync(queue_dev, 0, sizeof(int), st);
     if (e) return e;
@@ -872,7 +887,7 @@ int engine_batch(const Solve *solves_dev, const int *ncolours_dev, int count, co
                                 max_iter, grid, st);
     if (e) return e;
     k_batch_finish<<<(count + 127) / 128, 128, 0, st>>>(solves_dev, ncolours_dev, count, logdet_dev,
-                                                       seed_dev, flag_dev, iters_dev);
+                                                       seed_dev, flag_dev, iters_dev, tile_passes_dev);
     return (int)cudaGetLastError();
 }
 

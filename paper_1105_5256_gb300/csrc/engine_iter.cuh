@@ -4,6 +4,7 @@
 #include "engine_csr.cuh"
 #include "engine_device.cuh"
 #include "engine_lean.cuh"
+#include "engine_lean3d.cuh"
 
 namespace ld {
 
@@ -12,6 +13,37 @@ template <typename V, int T, int KIND>
 constexpr bool has_lean() {
     return std::is_same<V, float>::value && (T == 2 || T == 4) &&
            (KIND == KIND_2D5 || KIND == KIND_2D13_SQ);
+}
+
+// the lean 3D pass: FP32 vectors, tiles of 2 or 4 columns, the 7-point kind
+template <typename V, int T, int KIND>
+constexpr bool has_lean3d() {
+    return std::is_same<V, float>::value && (T == 2 || T == 4) && KIND == KIND_3D7;
+}
+
+template <int T>
+int lean3d_launch(const Solve &s, dim3 grid, int cur, cudaStream_t st) {
+    constexpr size_t sm = lean3d_smem_bytes<float, T>();
+    if (s.keep_x0)
+        k_lean3d<float, T, true><<<grid, L3T, sm, st>>>(s, cur);
+    else
+        k_lean3d<float, T, false><<<grid, L3T, sm, st>>>(s, cur);
+    return (int)cudaGetLastError();
+}
+
+template <int T>
+int lean3d_occupancy(int *out, bool keepx) {
+    constexpr size_t sm = lean3d_smem_bytes<float, T>();
+    if (cudaFuncSetAttribute(k_lean3d<float, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_lean3d<float, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
+            cudaSuccess)
+        return (int)cudaGetLastError();
+    if (keepx)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_lean3d<float, T, true>, L3T, sm);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_lean3d<float, T, false>, L3T, sm);
+    return (int)cudaGetLastError();
 }
 
 template <int T, int X, int KIND>
@@ -54,6 +86,9 @@ struct IterLauncher {
         const int nt = s.tile0 < s.ntiles ? (s.ntiles - s.tile0 + ts - 1) / ts : 0;
         if (nt == 0) return 0;
         dim3 grid(s.bpt, nt);
+        if constexpr (has_lean3d<V, T, KIND>()) {
+            if (s.lean == LEAN_3D) return lean3d_launch<T>(s, grid, cur, st);
+        }
         if constexpr (has_lean<V, T, KIND>()) {
             if (s.lean == 1) return lean_launch<T, 1, KIND>(s, grid, cur, st);
             if constexpr (T == 2) {
@@ -91,6 +126,9 @@ struct OccLauncher {
     // resident CTAs per SM of the iteration kernels (the smaller of the two phases)
     static int run(int *out, bool bulk, int lean, bool keepx) {
         int a = 0, b = 0;
+        if constexpr (has_lean3d<V, T, KIND>()) {
+            if (lean == LEAN_3D) return lean3d_occupancy<T>(out, keepx);
+        }
         if constexpr (has_lean<V, T, KIND>()) {
             if (lean == 1) return lean_occupancy<T, 1, KIND>(out, keepx);
             if constexpr (T == 2) {

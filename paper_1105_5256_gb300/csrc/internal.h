@@ -125,7 +125,8 @@ int engine_modev(const Solve &s, int which, int nxt, double2 *psig, double *y, v
 int engine_batch_occupancy(int precision, int T);
 int engine_batch(const Solve *solves_dev, const int *ncolours_dev, int count, const int2 *items_dev,
                  int nitems, int *queue_dev, int max_iter, int precision, int T, int grid,
-                 double *logdet_dev, double *seed_dev, int *flag_dev, int *iters_dev, void *stream);
+                 double *logdet_dev, double *seed_dev, int *flag_dev, int *iters_dev, int *tile_passes_dev,
+                 void *stream);
 int engine_finish(const Solve &s, int col_begin, int col_end, void *stream);
 int engine_apply(const Operator &op, int precision, int T, int ntiles, const void *x, void *y,
                  void *stream);
