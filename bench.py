@@ -153,18 +153,18 @@ def pass_kernel_sha256(names=("engine_device.cuh", "engine_lean.cuh")):
     return h.hexdigest()
 
 
-def recorded_traffic(profile):
-    """DRAM bytes (read + write) of one CG pass from a committed ncu summary under
-    profiles/, or None when the pass kernels' sources changed since that capture (or the
-    summary is missing)."""
+def recorded_traffic(profile, key="traffic_bytes_per_pass"):
+    """DRAM bytes (read + write) of one CG pass (or, key traffic_bytes_per_vertex_tile_pass,
+    of one vertex and tile of a pass) from a committed ncu summary under profiles/, or None
+    when the pass kernel's sources changed since that capture (or the summary is missing)."""
     path = os.path.join(ROOT, "profiles", profile)
     try:
         rec = dict(line.split(": ", 1) for line in open(path).read().splitlines()
-                   if line.startswith(("engine_sha256: ", "engine_sources: ", "traffic_bytes_per_pass: ")))
+                   if line.startswith(("engine_sha256: ", "engine_sources: ", key + ": ")))
         names = tuple(rec.get("engine_sources", "engine_device.cuh engine_lean.cuh").split())
         if rec.get("engine_sha256", "").strip() != pass_kernel_sha256(names):
             return None
-        return float(rec["traffic_bytes_per_pass"])
+        return float(rec[key])
     except (OSError, KeyError, ValueError):
         return None
 
@@ -286,8 +286,13 @@ def config_field3d(L, side, steps, peak, src, fp64=True, T=0):
     info = r["info"]
     T = info["tile_width"]
     lean = r["info"]["pass_words"] == 6
+    traffic = None
+    if lean and T == 4:   # the 96^3 capture's bytes per vertex and tile, over this run's tile-passes
+        per = recorded_traffic("k_lean3d_field96_T4.md", "traffic_bytes_per_vertex_tile_pass")
+        traffic = per * n * r["tile_iters"] / max(r["passes"], 1) if per else None
     roof = roofline_entry("k_lean3d (7-point, lean, seed solution kept)" if lean else
-                          "k_stream3d (7-point, stored w, seed solution kept)", n, T, 4, r, True, 4 * n, peak, src)
+                          "k_stream3d (7-point, stored w, seed solution kept)", n, T, 4, r, True, 4 * n, peak, src,
+                          traffic=traffic)
     out = {"workload": "Dirichlet %d^3, 7-point, kappa^2 field, d=6, N=32, tol 1e-6, grad c" % side,
            "value": steps / (r["ms"] / 1e3), "unit": UNIT, "evaluations": steps,
            "dtype": "f32 vectors / f64 scalars", "n_colours": info["n_colours"], "tile_width": T,
