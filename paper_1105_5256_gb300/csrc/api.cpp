@@ -5,6 +5,7 @@
 // "eq_rat_app"), device buffers, the CG iteration driver (CUDA-graph chunks
 // with an on-device convergence counter) and the gradient pass.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -19,6 +20,7 @@
 #include <new>
 #include <sstream>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -1743,6 +1745,9 @@ ld_status ld_grid_bounds(const ld_matrix *Q, double *lmin, double *lmax) {
 // Build a batch context with tile width T.  step_s: seconds of one CTA step (one lattice
 // row of 128 vertices) of the persistent engine, from the tuner's measurement; an instance
 // whose one-CTA solve would outlast the batch runs on the grid engine (step_s <= 0: none).
+// host threads driving a batch's grid-engine instances at once
+constexpr int kBatchLargeThreads = 8;
+
 ld_status batch_build(int count, const ld_matrix *Qs, const int *distances, int n_shifts, double tol,
                       const ld_options &opt, int T, double step_s, ld_ctx **out) {
     ld_ctx *c = new (std::nothrow) ld_ctx();
@@ -1949,28 +1954,46 @@ ld_status ld_batch_logdet(ld_ctx *c, double *logdets, double *grads, ld_info *in
     const auto t0 = std::chrono::steady_clock::now();
     // the persistent launch for the small instances first (asynchronous) ...
     if (nsmall > 0) CUDA_TRY(cudaGraphLaunch(c->bgraph, c->stream));
-    // ... then the large ones, each across the GPU on its own stream
-    std::vector<double> lval(c->large_idx.size()), lseed(c->large_idx.size());
+    // ... then the large ones, each across the GPU on its own stream; up to kLargeThreads
+    // host threads drive them at once (a solve waits on its own stream between chunks of
+    // passes, so one host thread per instance keeps several instances' passes in flight)
+    const size_t nl = c->large_idx.size();
+    std::vector<double> lval(nl), lseed(nl);
+    std::vector<ld_info> linfo(nl);
+    std::vector<ld_status> lst(nl, LD_OK);
+    std::vector<std::string> lmsg(nl);
+    std::atomic<size_t> next{0};
+    auto worker = [&]() {
+        for (size_t k = next++; k < nl; k = next++) {
+            ld_ctx *sc = c->subs[c->large_idx[k]];
+            double o[2] = {0.0, 0.0};
+            std::memset(&linfo[k], 0, sizeof linfo[k]);
+            lst[k] = run_solve(sc, 0, sc->ncolours, false, o, &linfo[k]);
+            if (lst[k] != LD_OK) lmsg[k] = g_err;   // this thread's message
+            lval[k] = o[0];
+            lseed[k] = o[1];
+        }
+    };
+    const size_t nth = std::min(nl, (size_t)kBatchLargeThreads);
+    if (nth <= 1) {
+        worker();
+    } else {
+        std::vector<std::thread> pool;
+        for (size_t k = 0; k < nth; ++k) pool.emplace_back(worker);
+        for (std::thread &th : pool) th.join();
+    }
     int iters = 0;
     int64_t tile_iters = 0, vertex_tile_iters = 0, launches = nsmall > 0 ? 3 : 0;
     ld_status st = LD_OK;
-    for (size_t k = 0; k < c->large_idx.size() && st == LD_OK; ++k) {
-        ld_ctx *sc = c->subs[c->large_idx[k]];
-        double o[2] = {0.0, 0.0};
-        ld_info si;
-        std::memset(&si, 0, sizeof si);
-        ld_status s1 = run_solve(sc, 0, sc->ncolours, false, o, &si);
-        if (s1 != LD_OK) {
-            std::string msg = g_err;
-            st = fail(s1, "instance %d: %s", c->large_idx[k], msg.c_str());
-            break;
+    for (size_t k = 0; k < nl; ++k) {
+        if (lst[k] != LD_OK) {
+            if (st == LD_OK) st = fail(lst[k], "instance %d: %s", c->large_idx[k], lmsg[k].c_str());
+            continue;
         }
-        lval[k] = o[0];
-        lseed[k] = o[1];
-        iters = std::max(iters, (int)si.iters);
-        tile_iters += si.tile_iters;
-        vertex_tile_iters += si.vertex_tile_iters;
-        launches += si.gpu_launches;
+        iters = std::max(iters, (int)linfo[k].iters);
+        tile_iters += linfo[k].tile_iters;
+        vertex_tile_iters += linfo[k].vertex_tile_iters;
+        launches += linfo[k].gpu_launches;
     }
     if (nsmall > 0) {
         CUDA_TRY(cudaMemcpyAsync(out.data(), c->d_bout.p, sizeof(double) * 2 * nsmall, cudaMemcpyDeviceToHost, c->stream));

@@ -73,9 +73,10 @@ struct Solve {
     int bpt;               // CTAs per tile (grid engine)
     int strips, seg;       // 2D kinds: lattice strips per tile, rows per CTA segment
     int bulk;              // 2D kinds: rows arrive by bulk (TMA) copies (alignment permits)
-    int lean;              // 2D kinds, FP32: 0 the stored-w pass (state r, w, p); X > 0 the
+    int lean;              // FP32: 0 the stored-w pass (state r, w, p); 2D kinds X = 1, 2 the
                            // lean pass (state r and p, or r and u = Q1 p for the Matern
-                           // kind; w recomputed), X lattice columns per thread
+                           // kind; w recomputed), X lattice columns per thread; 3 the lean
+                           // 3D pass
     const uint8_t *lane;   // lean pass: per-tile lane codes in strip layout (or null)
     int lane_mask;         // lean pass, 5-point, scalar kappa^2 with a mask: the codes' high
                            // bit is the mask bit (diagonal kappa^2 + tau mask_i formed in the pass)
