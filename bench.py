@@ -21,6 +21,12 @@ from __future__ import annotations
 import argparse
 import json
 import os
+
+# concurrent tile groups and batch instances each need a hardware queue of their own; the
+# CUDA runtime's default of 8 makes streams beyond the eighth wait on one another (read when
+# the CUDA context is created, so set before torch touches the device)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 import statistics
 import subprocess
 import sys

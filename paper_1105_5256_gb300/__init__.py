@@ -18,6 +18,12 @@ from __future__ import annotations
 import ctypes as C
 import os
 
+# The grid engine runs tile groups, and a batch its large instances, on streams of their own;
+# the CUDA runtime serves 8 hardware queues unless told otherwise, and streams beyond the
+# eighth then wait on one another.  The setting is read when the process creates its CUDA
+# context, so it takes effect when this package is imported first.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 import numpy as np
 
 from ._build import OUT as _LIB_PATH

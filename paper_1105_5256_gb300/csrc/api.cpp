@@ -1795,6 +1795,14 @@ ld_status batch_build(int count, const ld_matrix *Qs, const int *distances, int 
         c->subs.push_back(sc);
         (large ? c->large_idx : c->small_idx).push_back(i);
     }
+    // the grid-engine instances run kBatchLargeThreads at a time: each plans for its share
+    const int share = std::min((int)c->large_idx.size(), kBatchLargeThreads);
+    for (int i : c->large_idx) {
+        ld_ctx *sc = c->subs[i];
+        sc->s.share = share;
+        ld::engine_plan(sc->s);
+        invalidate_graph(sc);
+    }
     // device table of the small instances' solves and their work items, longest first
     const int nsmall = (int)c->small_idx.size();
     std::vector<Solve> solves(std::max(nsmall, 1));

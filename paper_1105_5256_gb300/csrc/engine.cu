@@ -805,6 +805,9 @@ int engine_plan(Solve &s) {
     // streams) 1.5 waves, so that CTAs of one group fill the gaps of another
     int64_t target = (int64_t)sms * occ;
     if (s.ntiles >= 2 && s.op.kind != KIND_CSR) target = target * 3 / 2;
+    // several solves at once (a batch's grid-engine instances): each takes its share, in
+    // longer row segments rather than more CTAs of a few rows each
+    if (s.share > 1) target = std::max<int64_t>(1, target / s.share);
     s.strips = 1;
     s.seg = 1;
     if (lattice2d) {

@@ -73,6 +73,8 @@ struct Solve {
     int bpt;               // CTAs per tile (grid engine)
     int strips, seg;       // 2D kinds: lattice strips per tile, rows per CTA segment
     int bulk;              // 2D kinds: rows arrive by bulk (TMA) copies (alignment permits)
+    int share;             // solves running on the device at once (a batch's grid-engine
+                           // instances): the plan sizes a launch for 1/share of it (<= 1: all)
     int lean;              // FP32: 0 the stored-w pass (state r, w, p); 2D kinds X = 1, 2 the
                            // lean pass (state r and p, or r and u = Q1 p for the Matern
                            // kind; w recomputed), X lattice columns per thread; 3 the lean
