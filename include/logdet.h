@@ -377,8 +377,14 @@ ld_status ld_grid_bounds(const ld_matrix *Q, double *lmin, double *lmax);
 /* Batched evaluation of many independent grid GMRFs of uneven size in one persistent
  * launch (each (instance, tile) a work item).  Qs[count] (grid kinds), distances[count]
  * as in ld_create; every instance gets its own colouring, spectral bounds and nodes.
- * opt: precision, max_iter, tile_width (0 = 2 for mixed, 1 for FP64), cuda_stream.
- * Errors: as ld_create, reported with the failing instance's index. */
+ * opt: precision, max_iter, tile_width (0 = chosen by timing short runs of the persistent
+ * launch per candidate, cached per batch shape), cuda_stream.  An instance whose one-CTA
+ * solve would outlast the batch (estimated from its size, its condition number and the
+ * measured time of a CTA step) runs on the multi-CTA grid engine instead, several at once
+ * on their own streams from host threads; for those to overlap, the process should set
+ * CUDA_DEVICE_MAX_CONNECTIONS=32 (or more) before it creates its CUDA context (the Python
+ * binding does so on import).  Errors: as ld_create, reported with the failing instance's
+ * index. */
 ld_status ld_batch_create(int count, const ld_matrix *Qs, const int *distances, int n_shifts,
                           double tol, const ld_options *opt, ld_ctx **out);
 
@@ -387,7 +393,9 @@ ld_status ld_batch_create(int count, const ld_matrix *Qs, const int *distances, 
  * NaN for the others; grads and info may be NULL.  One CUDA-graph launch: a queue
  * reset, a per-instance prep kernel, the persistent solve (CTAs pull (instance, tile)
  * items, longest first, and run each tile's whole CG-M in one CTA) and a per-instance
- * sum.  Errors: the first failing instance's status (no outputs written). */
+ * sum; beside it the grid-engine instances.  info: ms is the host wall time of the whole
+ * batch, tile_iters and vertex_tile_iters the exact passes every tile ran.  Errors: the
+ * first failing instance's status (no outputs written). */
 ld_status ld_batch_logdet(ld_ctx *ctx, double *logdets, double *grads, ld_info *info);
 
 /* ---------------------------------------------------------------------------
