@@ -213,8 +213,9 @@ typedef int (*ld_dmatvec_fn)(void *user, int32_t param, int64_t n, int32_t ncols
  * r, p, w (and x with keep_x0 or a gradient) on the device; the seed system Q x = v_c is
  * followed to the tolerance like the shifted ones, so ld_column_terms reports its
  * projections.  ld_logdet, ld_logdet_partial, ld_logdet_grad and ld_grad (after
- * ld_matfree_set_derivative), ld_column_terms, ld_logmv, ld_invsqrt_mv, ld_get_colouring,
- * ld_get_nodes and ld_destroy accept the context; the rest return LD_EUNSUPPORTED.
+ * ld_matfree_set_derivative), ld_column_terms, ld_logmv, ld_invsqrt_mv, ld_hutchinson,
+ * ld_get_colouring, ld_get_nodes and ld_destroy accept the context; the rest return
+ * LD_EUNSUPPORTED.
  * Errors: LD_EINVAL (checked before any device call), LD_EUNSUPPORTED, LD_ENOMEM,
  * LD_ECUDA; the solves add LD_ECALLBACK, LD_ENOTSPD, LD_ENOTCONV, LD_ENUMERIC. */
 ld_status ld_create_matfree(int64_t n, ld_matvec_fn matvec, void *user, const int32_t *colouring,

@@ -1592,6 +1592,7 @@ ld_status ld_select_distance(ld_ctx *c, int64_t j, double eps, int max_d, int32_
                              double *profile, ld_info *info) {
     if (!c || !distance) return fail(LD_EINVAL, "bad arguments");
     if (c->is_batch) return fail(LD_EINVAL, "batched context");
+    REJECT_MATFREE(c);   // graph distances need the operator's pattern
     if (j < 0 || j >= c->n) return fail(LD_EINVAL, "vertex %lld out of range", (long long)j);
     if (!(eps > 0.0) || !std::isfinite(eps)) return fail(LD_EINVAL, "eps must be > 0");
     if (max_d < 0 || max_d > 4096) return fail(LD_EINVAL, "max_d must be in [0, 4096]");

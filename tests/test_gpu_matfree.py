@@ -238,3 +238,11 @@ def test_matfree_vector_form_matches_dense_functions(ncols):
     # the probing solve still works after the vector form reused the buffers
     val, _ = L.ld_logdet(ctx)
     assert np.isfinite(val)
+    # Hutchinson's estimator runs on the same vector form: the sample mean of z^T log(Q) z
+    if ncols == 3:
+        est, se, samples, _ = L.ld_hutchinson(ctx, Vb)
+        assert np.all(np.abs(samples - np.sum(Vb * ref, axis=0)) <= 1e-7 * np.sum(np.abs(Vb * ref), axis=0))
+        assert abs(est - samples.mean()) <= 1e-12 * abs(samples).max()
+    with pytest.raises(L.LogDetError) as e:
+        L.ld_select_distance(ctx, 0, 1e-3)
+    assert e.value.status == L.LD_EUNSUPPORTED
