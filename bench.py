@@ -488,6 +488,20 @@ def run_small_configs(args):
         print(json.dumps(line), flush=True)
 
 
+def run_periodic64(args):
+    """configs[0] alone (the 64^2 torus as CSR, FP64), one JSON line."""
+    import torch
+    import paper_1105_5256_gb300 as L
+    torch.cuda.set_device(0)
+    L.library(build_if_missing=True)
+    r = config_periodic64(L, max(args.steps, 1))
+    line = {"metric": "log-det evals/sec (64^2 periodic 5-point as CSR, d=4, N=20, FP64)", "value": r.pop("value"),
+            "unit": UNIT, "n_gpus": 1, "steps": r["evaluations"], "warmup": 2, "higher_is_better": True,
+            "dtype": r.pop("dtype"), "data": "synthetic", "config": {"workload": r.pop("workload")}}
+    line.update(r)
+    print(json.dumps(line), flush=True)
+
+
 def run_posterior(args):
     """configs[3] alone (the 2048^2 posterior, mixed with reliable updates, gradient), one
     JSON line; `--steps 1 --warmup 0 --fp64-sample 0` runs a single evaluation."""
@@ -826,7 +840,8 @@ def main():
     ap.add_argument("--split", default="batches", choices=["batches", "colours"],
                     help="several GPUs: independent batches per rank, or every evaluation's colours split")
     ap.add_argument("--workload", default="matern1024",
-                    choices=["matern1024", "batch256", "field3d256", "small", "posterior2048", "mesh1024"])
+                    choices=["matern1024", "batch256", "field3d256", "small", "posterior2048", "mesh1024",
+                             "periodic64"])
     ap.add_argument("--side", type=int, default=256,
                     help="grid side (field3d256 workload) or mesh vertices a side (mesh1024, 256 = 1024)")
     ap.add_argument("--fp64-sample", type=int, default=2,
@@ -846,6 +861,8 @@ def main():
         run_posterior(args)
     elif args.workload == "mesh1024":
         run_mesh(args)
+    elif args.workload == "periodic64":
+        run_periodic64(args)
     else:
         run_ours(args)
 
