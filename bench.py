@@ -358,7 +358,12 @@ def config_mesh(L, side, steps, peak, src, matfree=True, fp64=True, T=0):
     info = m["info"]
     T = info["tile_width"]
     # the matrix once per pass: nnz (4-byte index + 4-byte value) + the 8-byte row pointer
-    roof = roofline_entry("k_csr_step + k_csr_spmv (CSR)", n, T, 4, m, False, nnz * 8 + 8 * n, peak, src)
+    traffic = None
+    if T == 4:   # the 512^2 capture's bytes per vertex and tile, over this run's tile-passes
+        per = recorded_traffic("k_csr_spmv_mesh512_T4.md", "traffic_bytes_per_vertex_tile_pass")
+        traffic = per * n * m["tile_iters"] / max(m["passes"], 1) if per else None
+    roof = roofline_entry("k_csr_step + k_csr_spmv (CSR)", n, T, 4, m, False, nnz * 8 + 8 * n, peak, src,
+                          traffic=traffic)
     res = {"workload": "perturbed %dx%d-vertex triangulation, P1 FEM SPDE alpha=2, kappa^2 h^2 0.1, "
                        "d=2, N=20, tol 1e-6" % (side, side),
            "value": steps / (m["ms"] / 1e3), "unit": UNIT, "evaluations": steps,
@@ -420,6 +425,8 @@ def run_batch(args):
     out = {}
     peak, src = peak_hbm()
     for name, prec in (("mixed", L.LD_MIXED), ("fp64", L.LD_FP64)):
+        if name == "fp64" and args.fp64_sample <= 0:
+            continue
         b = L.ld_batch_create(mats, dists, NSHIFT, TOL, L.options(precision=prec))
         for _ in range(args.warmup):
             L.ld_batch_logdet(b)
@@ -442,17 +449,17 @@ def run_batch(args):
                                   "note": "whole batch wall time, both engines, over the active bytes"}}
         del b
     # 256 sequential FP64 evaluations, one context per instance (created beforehand)
-    ctxs = [L.ld_create(m, d, NSHIFT, TOL, L.options(precision=L.LD_FP64)) for m, d in zip(mats, dists)]
-    seq_ms = 0.0
-    seq_vals = []
-    for c in ctxs:
-        v, info = L.ld_logdet(c)
-        seq_ms += info["ms"]
-        seq_vals.append(v)
-    del ctxs
-    seq_vals = np.array(seq_vals)
-    rel = float(np.max(np.abs(out["mixed"]["vals"] - out["fp64"]["vals"]) / np.abs(out["fp64"]["vals"])))
-    rel_seq = float(np.max(np.abs(out["mixed"]["vals"] - seq_vals) / np.abs(seq_vals)))
+    seq_ms, seq_vals, rel, rel_seq = 0.0, [], None, None
+    if args.fp64_sample > 0:
+        ctxs = [L.ld_create(m, d, NSHIFT, TOL, L.options(precision=L.LD_FP64)) for m, d in zip(mats, dists)]
+        for c in ctxs:
+            v, info = L.ld_logdet(c)
+            seq_ms += info["ms"]
+            seq_vals.append(v)
+        del ctxs
+        seq_vals = np.array(seq_vals)
+        rel = float(np.max(np.abs(out["mixed"]["vals"] - out["fp64"]["vals"]) / np.abs(out["fp64"]["vals"])))
+        rel_seq = float(np.max(np.abs(out["mixed"]["vals"] - seq_vals) / np.abs(seq_vals)))
     line = {"metric": "log-det evals/sec (batch of 256 uneven 2D GMRFs, one persistent launch)",
             "value": out["mixed"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": out["mixed"]["ms_per_step"],
@@ -460,12 +467,13 @@ def run_batch(args):
             "dtype": "f32 vectors / f64 scalars", "data": "synthetic (seeded batch)",
             "config": {"workload": "256 grids, sides U{32..512}, 5-pt d=4 / 13-pt d=2, N=20, tol 1e-6",
                        "points": int(sum(i.n for i in insts)), "tile_width": out["mixed"]["tile_width"]},
-            "roofline": out["mixed"]["roofline"],
-            "fp64_form": {"value": out["fp64"]["value"], "ms_per_step": out["fp64"]["ms_per_step"],
-                          "mixed_vs_fp64_rel_diff_max": rel, "roofline": out["fp64"]["roofline"]},
-            "sequential_fp64": {"value": 256 / (seq_ms / 1e3), "ms": seq_ms,
-                                "note": "256 separate ld_logdet calls in FP64, one context per instance",
-                                "mixed_batch_vs_sequential_rel_diff_max": rel_seq}}
+            "roofline": out["mixed"]["roofline"]}
+    if args.fp64_sample > 0:
+        line["fp64_form"] = {"value": out["fp64"]["value"], "ms_per_step": out["fp64"]["ms_per_step"],
+                             "mixed_vs_fp64_rel_diff_max": rel, "roofline": out["fp64"]["roofline"]}
+        line["sequential_fp64"] = {"value": 256 / (seq_ms / 1e3), "ms": seq_ms,
+                                   "note": "256 separate ld_logdet calls in FP64, one context per instance",
+                                   "mixed_batch_vs_sequential_rel_diff_max": rel_seq}
     print(json.dumps(line), flush=True)
 
 
