@@ -399,7 +399,7 @@ def run_mesh(args):
     torch.cuda.set_device(0)
     L.library(build_if_missing=True)
     peak, src = peak_hbm()
-    side = args.side if args.side != 256 else 1024
+    side = args.side or 1024
     r = config_mesh(L, side, max(args.steps, 1), peak, src, matfree=args.fp64_sample > 0,
                     fp64=args.fp64_sample > 0, T=args.tile_width)
     line = {"metric": "log-det evals/sec (FEM SPDE alpha=2 on a %d^2-vertex mesh, CSR, d=2, N=20)" % side,
@@ -536,10 +536,11 @@ def run_field3d(args):
     clocks = Clocks()
     clocks.start()
     t0 = time.perf_counter()
-    r = config_field3d(L, args.side, args.steps, peak, src, fp64=args.fp64_sample > 0, T=args.tile_width)
+    side = args.side or 256
+    r = config_field3d(L, side, args.steps, peak, src, fp64=args.fp64_sample > 0, T=args.tile_width)
     wall = time.perf_counter() - t0
     clk = clocks.stop()
-    line = {"metric": "log-det+grad evals/sec (Dirichlet %d^3, 7-point, kappa^2 field, d=6, N=32)" % args.side,
+    line = {"metric": "log-det+grad evals/sec (Dirichlet %d^3, 7-point, kappa^2 field, d=6, N=32)" % side,
             "value": r.pop("value"), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": 1,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": r.pop("dtype"),
             "data": "synthetic (seeded kappa^2 field)", "config": {"workload": r.pop("workload")},
@@ -850,8 +851,9 @@ def main():
     ap.add_argument("--workload", default="matern1024",
                     choices=["matern1024", "batch256", "field3d256", "small", "posterior2048", "mesh1024",
                              "periodic64"])
-    ap.add_argument("--side", type=int, default=256,
-                    help="grid side (field3d256 workload) or mesh vertices a side (mesh1024, 256 = 1024)")
+    ap.add_argument("--side", type=int, default=0,
+                    help="grid side (field3d256 workload, default 256) or mesh vertices a side (mesh1024, "
+                         "default 1024)")
     ap.add_argument("--fp64-sample", type=int, default=2,
                     help="draws also evaluated in the plain FP64 form (mixed precision runs)")
     ap.add_argument("--kappa2", type=float, default=0.0,
