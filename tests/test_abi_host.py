@@ -310,3 +310,21 @@ def test_automatic_shift_count_meets_its_certificate_target():
         assert hht.certificate(lo, hi, s, a) > 0.5 * target
     with pytest.raises(L.LogDetError):
         L.ld_auto_shifts(2.0, 1.0)
+
+
+def test_package_import_requests_hardware_queues_for_its_streams():
+    """Importing the package asks the CUDA runtime for 32 hardware queues (tile groups and a
+    batch's concurrent instances run on streams of their own; with the default 8, streams
+    beyond the eighth wait on one another), unless the caller set a value."""
+    import subprocess
+    import sys
+    code = ("import os; os.environ.pop('CUDA_DEVICE_MAX_CONNECTIONS', None); "
+            "import paper_1105_5256_gb300; print(os.environ['CUDA_DEVICE_MAX_CONNECTIONS'])")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr[-500:]
+    assert out.stdout.strip() == "32"
+    code2 = "import paper_1105_5256_gb300, os; print(os.environ['CUDA_DEVICE_MAX_CONNECTIONS'])"
+    env = dict(os.environ, CUDA_DEVICE_MAX_CONNECTIONS="12")
+    out2 = subprocess.run([sys.executable, "-c", code2], cwd=ROOT, capture_output=True, text=True, timeout=300,
+                          env=env)
+    assert out2.returncode == 0 and out2.stdout.strip() == "12"
