@@ -223,7 +223,7 @@ def roofline_entry(kernel, n, T, word, r, keep_x, bq_per_pass, peak, src, traffi
 
 
 def config_posterior2048(L, steps, peak, src, warmup=1, fp64=True):
-    """configs[3]: Gauss-linear posterior Q_p = 0.1 I - Lap + 4 diag(mask) on 2048 x 2048
+    """The Gauss-linear posterior workload: Q_p = 0.1 I - Lap + 4 diag(mask) on 2048 x 2048
     (10 % observed, seeded), distance 4, N = 20, log det and gradient (kappa^2, tau) per
     evaluation; mixed precision with reliable updates (tol 1e-9) against the plain FP64
     form on the same problem."""
@@ -261,7 +261,7 @@ def config_posterior2048(L, steps, peak, src, warmup=1, fp64=True):
 
 
 def config_periodic64(L, steps):
-    """configs[0]: Q = 0.5 I - Lap on the 64 x 64 torus given as a CSR matrix, distance 4,
+    """The small CSR workload: Q = 0.5 I - Lap on the 64 x 64 torus given as a CSR matrix, distance 4,
     N = 20, tol 1e-10, FP64 (the one-CTA-per-tile engine: L2-resident, latency-bound)."""
     dims, k2 = (64, 64), 0.5
     rows, cols, w = synth.torus_edges(*dims)
@@ -279,7 +279,7 @@ def config_periodic64(L, steps):
 
 
 def config_field3d(L, side, steps, peak, src, fp64=True, T=0):
-    """configs[4]: Dirichlet side^3, 7-point, seeded kappa^2 field (log kappa^2 = -2 +
+    """The 3D field workload: Dirichlet side^3, 7-point, seeded kappa^2 field (log kappa^2 = -2 +
     smoothed N(0,1)), distance 6, N = 32, tol 1e-6, mixed precision; one evaluation = log
     det and its derivative with respect to the field's scale c (kappa^2 = c kappa0^2)."""
     dims = (side, side, side)
@@ -411,7 +411,7 @@ def run_mesh(args):
 
 
 def run_batch(args):
-    """configs[2]: 256 independent 2D GMRFs of uneven size (sides 32..512, 5-point d=4 or
+    """The batch workload: 256 independent 2D GMRFs of uneven size (sides 32..512, 5-point d=4 or
     13-point d=2, kappa^2 log-uniform) in one persistent launch per step; mixed precision,
     with the same batch in the plain FP64 form, and 256 sequential FP64 ld_logdet calls
     (one context per instance) beside it."""
@@ -478,7 +478,7 @@ def run_batch(args):
 
 
 def run_small_configs(args):
-    """configs[0] and configs[3], one JSON line each."""
+    """The small CSR workload and the 2048^2 posterior, one JSON line each."""
     import torch
     import paper_1105_5256_gb300 as L
     torch.cuda.set_device(0)
@@ -497,7 +497,7 @@ def run_small_configs(args):
 
 
 def run_periodic64(args):
-    """configs[0] alone (the 64^2 torus as CSR, FP64), one JSON line."""
+    """The 64^2 torus as CSR (FP64) alone, one JSON line."""
     import torch
     import paper_1105_5256_gb300 as L
     torch.cuda.set_device(0)
@@ -511,7 +511,7 @@ def run_periodic64(args):
 
 
 def run_posterior(args):
-    """configs[3] alone (the 2048^2 posterior, mixed with reliable updates, gradient), one
+    """The 2048^2 posterior alone (mixed with reliable updates, gradient), one
     JSON line; `--steps 1 --warmup 0 --fp64-sample 0` runs a single evaluation."""
     import torch
     import paper_1105_5256_gb300 as L
@@ -527,7 +527,7 @@ def run_posterior(args):
 
 
 def run_field3d(args):
-    """configs[4] (Dirichlet 256^3 by default, `--side` for smaller grids), one JSON line."""
+    """The 3D field (Dirichlet 256^3 by default, `--side` for smaller grids), one JSON line."""
     import torch
     import paper_1105_5256_gb300 as L
     torch.cuda.set_device(0)
