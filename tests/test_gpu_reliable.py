@@ -92,3 +92,35 @@ def test_true_residual_reported_only_with_seed_solutions(oracle):
                       L.options(precision=L.LD_MIXED, engine=1, colouring=oracle["col"]))
     _, info = L.ld_logdet(ctx)
     assert info["rel_resid_max"] == -1.0 and info["reliable_updates"] == 0
+
+
+def test_reliable_updates_on_the_csr_pass():
+    """The CSR pass (streaming step + row-group product) with reliable updates: an
+    ill-conditioned FEM alpha = 2 mesh precision Q = s Q0 (s = 2) in mixed precision.  The
+    scale gradient d log det / ds = sum_c v_c^T Q^{-1} Q0 v_c is n / s exactly for any
+    colouring, so its error measures the kept seed solutions: with updates the true residual
+    meets the tolerance and the gradient is FP64-accurate; without them it is not."""
+    import synth
+    p, t = synth.perturbed_triangulation(31, 60, 55)
+    h = 1.0 / 59
+    Q = om.fem_spde_precision(p, t, 0.01 / h ** 2, 2, 1.0)
+    n = Q.shape[0]
+    rp, ci, vv = om.csr_arrays(Q)
+    lo = 0.9 * float(spla.eigsh(Q.tocsc(), k=1, sigma=0.0, which="LM", return_eigenvectors=False)[0])
+    hi = float(np.abs(Q).sum(axis=1).max())
+    out = {}
+    for delta in (0.0, 1e-2):
+        ctx = L.ld_create(L.csr_matrix(rp, ci, vv, scale=2.0), 2, NSHIFT, TOL,
+                          L.options(precision=L.LD_MIXED, engine=1, tile_width=4, reliable_delta=delta,
+                                    lambda_min=2.0 * lo, lambda_max=2.0 * hi))
+        v, g, info = L.ld_logdet_grad(ctx, [L.LD_P_SCALE])
+        out[delta] = (v, float(g[0]), info)
+        assert info["engine"] == 1 and info["pass_words"] == 10
+    v1, g1, i1 = out[1e-2]
+    v0, g0, i0 = out[0.0]
+    print("CSR mixed: true residual %.2e -> %.2e with %d updates; grad rel err %.1e -> %.1e"
+          % (i0["rel_resid_max"], i1["rel_resid_max"], i1["reliable_updates"],
+             abs(g0 - n / 2) / (n / 2), abs(g1 - n / 2) / (n / 2)))
+    assert i1["reliable_updates"] >= 1 and i1["rel_resid_max"] <= 10 * TOL
+    assert abs(g1 - n / 2) <= 1e-6 * n / 2
+    assert abs(v1 - v0) <= 2e-5 * abs(v0)
