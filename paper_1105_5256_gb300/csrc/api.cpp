@@ -132,6 +132,7 @@ struct ld_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr, ev3 = nullptr;
+    cudaEvent_t evc[2] = {nullptr, nullptr};   // ends of the chunks in flight (two slots)
     cudaGraphExec_t graph = nullptr;
     int graph_chunk = 0;
     // grid engine: tile groups iterate on their own streams inside the captured graph
@@ -168,6 +169,8 @@ struct ld_ctx {
         if (ev1) cudaEventDestroy(ev1);
         if (ev2) cudaEventDestroy(ev2);
         if (ev3) cudaEventDestroy(ev3);
+        for (cudaEvent_t e : evc)
+            if (e) cudaEventDestroy(e);
         if (h_pinned) cudaFreeHost(h_pinned);
         for (int g = 0; g < kMaxGroups; ++g) {
             if (gstream[g]) cudaStreamDestroy(gstream[g]);
@@ -691,6 +694,42 @@ ld_status run_solve(ld_ctx *c, int cb, int ce, bool keep_x0, double out[2], ld_i
         float e = 0.f;
         CUDA_TRY(cudaEventElapsedTime(&e, c->ev2, c->ev3));
         iter_ms += e;
+    } else if (!ru) {
+        if (ld_status g = ensure_graph(c)) return g;
+        // One chunk queued ahead of the host: chunk k + 1 is launched before the host waits
+        // for chunk k's convergence count (pinned slot k mod 2), so the stream never drains
+        // between chunks.  A chunk launched after the solve converged finds every tile done
+        // and its kernels return at once.
+        int done_iters = 0, last = 0;
+        auto launch_chunk = [&](int slot) -> ld_status {
+            CUDA_TRY(cudaGraphLaunch(c->graph, c->stream));
+            CUDA_TRY(cudaMemcpyAsync(c->h_pinned + 2 * slot, c->s.remaining, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                     c->stream));
+            CUDA_TRY(cudaMemcpyAsync(c->h_pinned + 2 * slot + 1, c->s.status, sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(cudaEventRecord(c->evc[slot], c->stream));
+            // one launch per tile group and pass (two on CSR: the step and the product)
+            launches += (int64_t)c->chunk * std::max(c->ngroups, 1) * (c->kind == LD_CSR ? 2 : 1);
+            done_iters += c->chunk;
+            return LD_OK;
+        };
+        CUDA_TRY(cudaEventRecord(c->ev2, c->stream));
+        if (ld_status g = launch_chunk(0)) return g;
+        for (int k = 0;; ++k) {
+            const int slot = k & 1;
+            const bool more = done_iters < max_iter;
+            if (more)
+                if (ld_status g = launch_chunk(slot ^ 1)) return g;
+            CUDA_TRY(cudaEventSynchronize(c->evc[slot]));
+            last = slot;
+            if (c->h_pinned[2 * slot] <= 0 || c->h_pinned[2 * slot + 1] != 0 || !more) break;
+        }
+        // passes' time: from the first chunk to the end of the one that finished the solve
+        float e = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&e, c->ev2, c->evc[last]));
+        iter_ms += e;
+        c->h_pinned[0] = c->h_pinned[2 * last];
+        c->h_pinned[1] = c->h_pinned[2 * last + 1];
     } else {
         if (ld_status g = ensure_graph(c)) return g;
         int done_iters = 0;
@@ -1052,6 +1091,8 @@ ld_status ld_create(const ld_matrix *Q, int colouring_distance, int n_shifts, do
     CUDA_TRY(cudaEventCreate(&c->ev1));
     CUDA_TRY(cudaEventCreate(&c->ev2));
     CUDA_TRY(cudaEventCreate(&c->ev3));
+    CUDA_TRY(cudaEventCreate(&c->evc[0]));
+    CUDA_TRY(cudaEventCreate(&c->evc[1]));
     CUDA_TRY(cudaMallocHost((void **)&c->h_pinned, 4 * sizeof(int32_t)));
 
     // device copies of the problem
