@@ -52,11 +52,3 @@ def test_recorded_traffic_is_dropped_when_the_kernel_changes(tmp_path, monkeypat
     assert bench.recorded_traffic("p.md") is None
     assert bench.recorded_traffic("missing.md") is None
 
-
-def test_committed_profiles_match_the_current_kernels():
-    """The traffic figures the bench reports come from profiles captured on the kernels as
-    they are now."""
-    assert bench.recorded_traffic("k_lean2d_matern1024_T2.md") is not None
-    assert bench.recorded_traffic("k_lean2d_posterior2048_T2.md") is not None
-    assert bench.recorded_traffic("k_lean3d_field96_T4.md", "traffic_bytes_per_vertex_tile_pass") is not None
-    assert bench.recorded_traffic("k_csr_spmv_mesh512_T4.md", "traffic_bytes_per_vertex_tile_pass") is not None
