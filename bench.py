@@ -410,29 +410,24 @@ def run_mesh(args):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args):
+def config_batch(L, steps, warmup, peak, src, fp64=True):
     """The batch workload: 256 independent 2D GMRFs of uneven size (sides 32..512, 5-point d=4 or
     13-point d=2, kappa^2 log-uniform) in one persistent launch per step; mixed precision,
-    with the same batch in the plain FP64 form, and 256 sequential FP64 ld_logdet calls
+    with (fp64) the same batch in the plain FP64 form and 256 sequential FP64 ld_logdet calls
     (one context per instance) beside it."""
-    import torch
-    import paper_1105_5256_gb300 as L
-    torch.cuda.set_device(0)
-    L.library(build_if_missing=True)
     insts = synth.batch_instances(3, count=256)
     mats = [L.grid_matrix(i.kind, i.dims, i.kappa2) for i in insts]
     dists = [i.distance for i in insts]
     out = {}
-    peak, src = peak_hbm()
     for name, prec in (("mixed", L.LD_MIXED), ("fp64", L.LD_FP64)):
-        if name == "fp64" and args.fp64_sample <= 0:
+        if name == "fp64" and not fp64:
             continue
         b = L.ld_batch_create(mats, dists, NSHIFT, TOL, L.options(precision=prec))
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             L.ld_batch_logdet(b)
         ms = 0.0
         vti = 0
-        for _ in range(args.steps):
+        for _ in range(steps):
             vals, _, info = L.ld_batch_logdet(b)
             ms += info["ms"]
             vti += info["vertex_tile_iters"]
@@ -440,18 +435,23 @@ def run_batch(args):
         # the active bytes: 4 state words a vertex and column of every pass each tile ran
         alg = 4 * word * info["tile_width"] * vti
         achieved = alg / (ms / 1e3) / 1e9
-        out[name] = {"value": 256 * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+        out[name] = {"value": 256 * steps / (ms / 1e3), "ms_per_step": ms / steps,
                      "vals": vals, "tile_width": info["tile_width"],
                      "roofline": {"bound": "hbm", "kernel": "k_batch_solve + grid engine (large instances)",
                                   "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                                  "traffic": None, "algorithmic_bytes_per_step": alg / args.steps,
+                                  "traffic": None, "algorithmic_bytes_per_step": alg / steps,
                                   "peak_source": src,
                                   "note": "whole batch wall time, both engines, over the active bytes"}}
         del b
-    # 256 sequential FP64 evaluations, one context per instance (created beforehand)
-    seq_ms, seq_vals, rel, rel_seq = 0.0, [], None, None
-    if args.fp64_sample > 0:
+    res = {"workload": "256 grids, sides U{32..512}, 5-pt d=4 / 13-pt d=2, N=20, tol 1e-6",
+           "value": out["mixed"]["value"], "unit": UNIT, "evaluations": 256 * steps,
+           "ms_per_step": out["mixed"]["ms_per_step"], "dtype": "f32 vectors / f64 scalars",
+           "points": int(sum(i.n for i in insts)), "tile_width": out["mixed"]["tile_width"],
+           "roofline": out["mixed"]["roofline"]}
+    if fp64:
+        # 256 sequential FP64 evaluations, one context per instance (created beforehand)
         ctxs = [L.ld_create(m, d, NSHIFT, TOL, L.options(precision=L.LD_FP64)) for m, d in zip(mats, dists)]
+        seq_ms, seq_vals = 0.0, []
         for c in ctxs:
             v, info = L.ld_logdet(c)
             seq_ms += info["ms"]
@@ -460,20 +460,32 @@ def run_batch(args):
         seq_vals = np.array(seq_vals)
         rel = float(np.max(np.abs(out["mixed"]["vals"] - out["fp64"]["vals"]) / np.abs(out["fp64"]["vals"])))
         rel_seq = float(np.max(np.abs(out["mixed"]["vals"] - seq_vals) / np.abs(seq_vals)))
+        res["fp64_form"] = {"value": out["fp64"]["value"], "ms_per_step": out["fp64"]["ms_per_step"],
+                            "mixed_vs_fp64_rel_diff_max": rel, "roofline": out["fp64"]["roofline"]}
+        res["sequential_fp64"] = {"value": 256 / (seq_ms / 1e3), "ms": seq_ms,
+                                  "note": "256 separate ld_logdet calls in FP64, one context per instance",
+                                  "mixed_batch_vs_sequential_rel_diff_max": rel_seq}
+    return res
+
+
+def run_batch(args):
+    """The batch workload alone, one JSON line (`--fp64-sample 0` skips the FP64 arms)."""
+    import torch
+    import paper_1105_5256_gb300 as L
+    torch.cuda.set_device(0)
+    L.library(build_if_missing=True)
+    peak, src = peak_hbm()
+    r = config_batch(L, args.steps, args.warmup, peak, src, fp64=args.fp64_sample > 0)
     line = {"metric": "log-det evals/sec (batch of 256 uneven 2D GMRFs, one persistent launch)",
-            "value": out["mixed"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": out["mixed"]["ms_per_step"],
+            "value": r.pop("value"), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r.pop("ms_per_step"),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 vectors / f64 scalars", "data": "synthetic (seeded batch)",
-            "config": {"workload": "256 grids, sides U{32..512}, 5-pt d=4 / 13-pt d=2, N=20, tol 1e-6",
-                       "points": int(sum(i.n for i in insts)), "tile_width": out["mixed"]["tile_width"]},
-            "roofline": out["mixed"]["roofline"]}
-    if args.fp64_sample > 0:
-        line["fp64_form"] = {"value": out["fp64"]["value"], "ms_per_step": out["fp64"]["ms_per_step"],
-                             "mixed_vs_fp64_rel_diff_max": rel, "roofline": out["fp64"]["roofline"]}
-        line["sequential_fp64"] = {"value": 256 / (seq_ms / 1e3), "ms": seq_ms,
-                                   "note": "256 separate ld_logdet calls in FP64, one context per instance",
-                                   "mixed_batch_vs_sequential_rel_diff_max": rel_seq}
+            "dtype": r.pop("dtype"), "data": "synthetic (seeded batch)",
+            "config": {"workload": r.pop("workload"), "points": r.pop("points"),
+                       "tile_width": r.pop("tile_width")}}
+    r.pop("unit")
+    r.pop("evaluations")
+    line.update(r)
     print(json.dumps(line), flush=True)
 
 
@@ -673,7 +685,8 @@ def run_ours(args):
         for key, fn in (("periodic64_csr_fp64", lambda: config_periodic64(L, 10)),
                         ("posterior2048_mixed_grad", lambda: config_posterior2048(L, 3, peak, src)),
                         ("field3d256_mixed_grad", lambda: config_field3d(L, 256, 1, peak, src)),
-                        ("mesh1024_csr_mixed", lambda: config_mesh(L, 1024, 2, peak, src))):
+                        ("mesh1024_csr_mixed", lambda: config_mesh(L, 1024, 2, peak, src)),
+                        ("batch256_mixed", lambda: config_batch(L, 2, 1, peak, src, fp64=False))):
             try:
                 oc[key] = fn()
             except Exception as e:      # a failing side configuration must not lose the headline
